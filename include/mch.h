@@ -1,0 +1,180 @@
+/*
+ * mch.h - C ABI of the GB300 (sm_103a) hierarchical multicontinuum cell-problem solver.
+ *
+ * What it computes (arXiv 2503.01276):
+ *   For every macropoint x_p of every level n of a nested macrogrid (Sec. 3.1, Eq. defi_Sn),
+ *   the R = N (1 + d) constrained cell functions Phi_p (Sec. 2, Eqs. phi_avar and phi_grad,
+ *   in the energy form of Sec. 3, Eq. phi_abstract): minimise 1/2 int kappa |grad v|^2 over
+ *   Q1 finite-element functions on the RVE Y+ = [-l/2, l/2]^d that vanish on its boundary,
+ *   subject to int_{R_q} psi_j v = delta_ij int_{R_q} psi_j          (constant functions)
+ *   and        int_{R_q} psi_j v = delta_ij int_{R_q} (x_m - c_mj) psi_j (linear functions)
+ *   for every continuum j and every sub-block R_q (the P^d periods of the RVE).
+ *   At level n > 1 the function is the interpolation of the parents' functions plus a
+ *   correction solved on the level's coarser grid (Sec. 3.3, Eqs. PhiXiI, phiXiI_all,
+ *   phi_avar_corrector, phi_grad_corrector). The effective coefficients are the energy Gram
+ *   of the cell functions (Sec. 2, Eq. Bs_defi), reported as
+ *       E[p][r][s] = (1/|R_p|) int_{R_p} kappa grad Phi_r . grad Phi_s,
+ *   with R_p = Y+ (no oversampling); the caller multiplies by |K_p|. Cell function r is
+ *   phi_i for r = i < N and phi_i^m for r = N + i d + m.
+ *
+ * Conventions:
+ *   - Macro indices run over [0, macro_n)^d; level n contains the indices that are multiples
+ *     of level_stride[n-1] along every axis and not in an earlier level. Points of a level
+ *     are ordered lexicographically with x fastest.
+ *   - Level n uses an RVE grid of n_fine / eta^(n-1) elements per side. Element fields are
+ *     stored per point as [n^d] with x fastest; kappa is FP64, labels are uint8 continuum
+ *     indices in [0, n_cont).
+ *   - Every pointer argument may be host memory or device memory of the current device; the
+ *     library detects which and stages host buffers through its own device buffers (the
+ *     copies are counted by mch_level_stats). All work is enqueued on the stream given to
+ *     mch_create and each call synchronises that stream once before returning its status.
+ *   - The library owns its workspaces and the cell functions of every level; the caller owns
+ *     every buffer it passes in.
+ *   - Level n may only be solved after levels 1..n-1 (MCH_ERR_ORDER otherwise).
+ */
+#ifndef MCH_H
+#define MCH_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mch_handle mch_handle;
+
+typedef enum {
+  MCH_OK = 0,
+  MCH_ERR_ARG = 1,            /* invalid argument or descriptor                      */
+  MCH_ERR_CUDA = 2,           /* a CUDA call failed (see mch_last_error)              */
+  MCH_ERR_OOM = 3,            /* device allocation failed                             */
+  MCH_ERR_ORDER = 4,          /* a level was solved before its parent levels          */
+  MCH_ERR_NOT_CONVERGED = 5,  /* iteration or refinement cap reached above rtol       */
+  MCH_ERR_BREAKDOWN = 6,      /* non-positive curvature or non-finite value in PCG    */
+  MCH_ERR_DEGENERATE = 7,     /* singular constraint Gram, kappa <= 0, empty continuum */
+  MCH_ERR_UNSUPPORTED = 8     /* a size this build has no kernel for                  */
+} mch_status;
+
+enum { MCH_FP64 = 0, MCH_MIXED = 1 };
+
+typedef struct {
+  int dim;                  /* d: 2 (3 is not built yet: MCH_ERR_UNSUPPORTED)               */
+  int n_cont;               /* N: continua, 1..4                                            */
+  int n_levels;             /* L                                                            */
+  int eta;                  /* FE coarsening factor between levels (Sec. 3.2)               */
+  int macro_n;              /* macro indices per axis on T_L                                */
+  const int *level_stride;  /* [n_levels] stride of T_n in macro-index units, last = 1      */
+  int n_fine;               /* elements per RVE side at level 1                             */
+  int periods;              /* P: sub-blocks R_q per side; n_level / P must be >= 2         */
+  int overs;                /* oversampling layers o; only 0 is built (MCH_ERR_UNSUPPORTED) */
+  double rve_len;           /* l: RVE side length                                           */
+  int precision;            /* MCH_MIXED (FP32 PCG inside FP64 refinement) or MCH_FP64      */
+  double rtol;              /* stop when sqrt(r'M^-1 r / r0'M^-1 r0) < rtol for the FP64
+                               projected residual (0 -> 1e-8). A child's coefficients inherit
+                               the error of its parents' functions to first order (about
+                               rtol); a level's own coefficients are quadratic in its error */
+  double inner_tol;         /* per-sweep PCG reduction of the same norm (0 -> 1e-4)         */
+  int max_iter;             /* PCG iterations per sweep (0 -> 4 n_level + 50)               */
+  int max_refine;           /* refinement sweeps (0 -> 6)                                   */
+  int keep_parents;         /* 1: keep every level's cell functions on the level-1 grid
+                               (needed by mch_backward); 0: keep only what children need    */
+} mch_desc;
+
+typedef struct {
+  int n_points;             /* points of the level                                  */
+  int n_elem;               /* elements per RVE side on this level                  */
+  int sweeps;               /* refinement sweeps used (max over the level)          */
+  int max_iters;            /* largest PCG iteration count of one (point, function) */
+  long long total_iters;    /* sum of PCG iterations over (point, function, sweep)  */
+  double max_relres;        /* largest final FP64 projected residual ratio          */
+  int n_dropped_rows;       /* constraint rows of empty (continuum, sub-block) pairs */
+  int gpu_launches;         /* kernels launched by the last mch_solve_level         */
+  long long h2d_bytes;      /* bytes staged host->device by the last call           */
+  long long d2h_bytes;      /* bytes staged device->host by the last call           */
+  /* Filled only while timing is enabled (mch_set_timing): CUDA-event times on the handle's
+   * stream of each phase of the last mch_solve_level, in milliseconds.                    */
+  double setup_ms;          /* constraint data                                      */
+  double interp_ms;         /* interpolation and correction right-hand sides        */
+  double pcg_ms;            /* all PCG sweep launches                               */
+  double prep_ms;           /* all FP64 refinement steps                            */
+  double final_ms;          /* effective coefficients and cell-function assembly    */
+  int pcg_launches;         /* PCG sweep launches                                   */
+  long long pcg_node_iters; /* sum over units of PCG iterations x interior nodes    */
+} mch_level_stats;
+
+/* Validates the descriptor, builds the level plan (Eq. defi_Sn; parents and multilinear
+ * weights of Sec. 3.3) on the host and allocates the per-level workspaces on the current
+ * device. `cuda_stream` is a cudaStream_t (NULL = legacy default stream). On failure *out
+ * is NULL and the status says why. */
+mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out);
+
+/* Host-only (no GPU work, no allocation on the device): the level plan of a descriptor.
+ * Writes the number of points of level `level` to *n_points and, for each non-NULL array,
+ * the macro indices [n_points][dim], parent levels (1-based, 0 = unused slot), parent
+ * positions and weights [n_points][2^dim]. Call with NULL arrays first to size them. */
+mch_status mch_plan_level(const mch_desc *desc, int level, int *n_points, int32_t *idx_out,
+                          int32_t *parent_level, int32_t *parent_pos, double *weight);
+
+/* Number of points of level `level` (1-based), or -1 for a bad handle/level. */
+int mch_level_num_points(const mch_handle *h, int level);
+
+/* Elements per RVE side of level `level`, or -1. */
+int mch_level_n_elem(const mch_handle *h, int level);
+
+/* Writes the macro indices of the level's points, [n_points][dim] int32, host memory. */
+mch_status mch_level_points(const mch_handle *h, int level, int32_t *idx_out);
+
+/* Writes the parents of the level's points: for point i, entries [i][0..2^dim) of
+ * parent_level (1-based, 0 = unused), parent_pos and weight (Sec. 3.3: sum of weights 1).
+ * Host memory, each array [n_points][2^dim]. */
+mch_status mch_level_parents(const mch_handle *h, int level, int32_t *parent_level,
+                             int32_t *parent_pos, double *weight);
+
+/* Solves all cell problems of level `level` (Algorithm 1, lines 4-6): builds the constraint
+ * data (Eqs. phi_avar, phi_grad), the interpolation of the parents and the correction
+ * right-hand sides (Eqs. phi_avar_corrector, phi_grad_corrector), runs the batched
+ * constrained solves, assembles Phi = I + Xi on the level-1 grid and reduces the effective
+ * coefficients (Eq. Bs_defi). kappa [n_points][n^d] FP64 > 0 and labels [n_points][n^d]
+ * uint8 (host or device). Status MCH_ERR_NOT_CONVERGED still leaves usable results whose
+ * residuals are reported by mch_level_stats. */
+mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const uint8_t *labels);
+
+/* Copies the level's effective coefficients E [n_points][R][R] FP64 to `E` (host or device).
+ * Optional outputs (NULL to skip): iters [n_points][R] int32 total PCG iterations, relres
+ * [n_points][R] FP64 final projected residual ratio. */
+mch_status mch_effective_coeffs(mch_handle *h, int level, double *E, int32_t *iters,
+                                double *relres);
+
+/* Copies the level's cell functions on the level-1 grid, [n_points][R][(n_fine+1)^d] FP64
+ * (node lattice including the zero boundary, x fastest), to `phi` (host or device). Needs
+ * keep_parents = 1 or a level that has children. */
+mch_status mch_cell_functions(mch_handle *h, int level, double *phi);
+
+/* Enables (1) or disables (0) CUDA-event timing of the phases of mch_solve_level (adds
+ * event records on the handle's stream; no extra synchronisation). */
+mch_status mch_set_timing(mch_handle *h, int enable);
+
+/* Statistics of the last mch_solve_level call on `level` (host struct). */
+mch_status mch_level_stats_get(const mch_handle *h, int level, mch_level_stats *out);
+
+/* Gradient of a scalar loss of the effective coefficients with respect to kappa of every
+ * element of every point of every level (adjoint of the constrained solves and of the
+ * interpolation, derived from the energy form of Eq. phi_abstract). dL_dE[n-1] points to
+ * [n_points][R][R] FP64, dL_dkappa[n-1] to [n_points][n^d] FP64 (host or device), for
+ * n = 1..L. Requires every level solved with keep_parents = 1. */
+mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const *dL_dkappa);
+
+/* Releases every library-owned buffer. Safe on NULL. */
+void mch_destroy(mch_handle *h);
+
+/* Text of the last error on this handle ("" if none). */
+const char *mch_last_error(const mch_handle *h);
+
+/* Status name, e.g. "MCH_ERR_ORDER". */
+const char *mch_status_name(mch_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MCH_H */

@@ -159,3 +159,41 @@ def run_hierarchy(wl, plan, media_levels, keep_phi=True, points=None):
         phis.append(Phi)
         out.append({"E": E, "Phi": Phi})
     return out
+
+
+def ancestors(plan, level: int, idx: int, acc=None):
+    """Set of (level, position) pairs needed to compute point `idx` of `level` (itself
+    and, recursively, its parents)."""
+    if acc is None:
+        acc = set()
+    if (level, idx) in acc:
+        return acc
+    acc.add((level, idx))
+    if level > 1:
+        for (lv, pos, _) in plan[level - 1]["parents"][idx]:
+            ancestors(plan, lv, pos, acc)
+    return acc
+
+
+def run_sampled(wl, plan, media_fn, targets):
+    """Algorithm 1 restricted to the listed (level, position) targets and their ancestors,
+    levels in order. media_fn(level, positions) -> (kappa, labels) for those points.
+    Returns {(level, position): solve_point result}."""
+    need = set()
+    for (lv, i) in targets:
+        ancestors(plan, lv, i, need)
+    out = {}
+    for lv in range(1, len(plan) + 1):
+        pos = sorted(i for (l, i) in need if l == lv)
+        if not pos:
+            continue
+        ops = LevelOps(wl, lv)
+        kap, lab = media_fn(lv, pos)
+        for k, i in enumerate(pos):
+            I = None
+            if lv > 1:
+                I = np.zeros((ops.gf.n_nodes, wl.n_rhs))
+                for (pl, pp, w) in plan[lv - 1]["parents"][i]:
+                    I += w * out[(pl, pp)]["Phi"].T
+            out[(lv, i)] = solve_point(ops, kap[k], lab[k], I)
+    return out

@@ -1,0 +1,562 @@
+// C ABI of the hierarchical multicontinuum cell-problem solver (declared in include/mch.h).
+//
+// Per level n (Algorithm 1, lines 4-6) mch_solve_level enqueues on the handle's stream:
+//   setup     per point: targets G, centroids, S = Ct M^-1 Ct^T and S^-1 (FP64)
+//   [n > 1]   I = sum_t c_t Phi_t on the level-1 grid (Eq. phiXiI_all), y = A_1 I with the
+//             child's medium prolonged (FP64), K_I = I^T A_1 I, b = -P^T y and
+//             g = G - C_1 I (Eqs. phi_avar_corrector, phi_grad_corrector)
+//   solve     FP64 refinement step, then up to max_refine x (PCG sweep + refinement step)
+//   E         |Y| E = K_I + 1/2 (Xi^T (A_n Xi - 2 b) + (A_n Xi - 2 b)^T Xi)   (Eq. Bs_defi)
+//   Phi       Phi = I + P Xi on the level-1 grid (Eq. PhiXiI)
+// and synchronises the stream once to read the per-unit convergence record.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mch.h"
+#include "common.cuh"
+#include "kernels.h"
+#include "plan.h"
+
+using namespace mch;
+
+namespace {
+
+struct Level {
+  LevelPlan plan;
+  int n = 0, rho = 1, npts = 0, nv = 0, nvf = 0;
+  double *kappa = nullptr;
+  uint8_t *labels = nullptr;
+  double *G = nullptr, *gI = nullptr, *Sinv64 = nullptr;
+  float *Sinv32 = nullptr;
+  double *x = nullptr, *b = nullptr;
+  double *rho0 = nullptr, *ratio = nullptr;
+  int *done = nullptr, *iters = nullptr, *ustat = nullptr, *pstat = nullptr, *dropped = nullptr;
+  double *E = nullptr, *phi = nullptr;
+  const double **par_ptr = nullptr;
+  double *par_w = nullptr;
+  bool solved = false;
+  mch_level_stats stats{};
+};
+
+}  // namespace
+
+struct mch_handle {
+  mch_desc d{};
+  std::vector<int> strides;
+  cudaStream_t st = nullptr;
+  int R = 0, nc = 0, nq = 0, slots = 0;
+  std::vector<Level> lv;
+  // scratch shared by the levels (solved one after another)
+  double *r64 = nullptr, *yfine = nullptr, *yc = nullptr;
+  void *vec = nullptr;
+  size_t vec_bytes = 0;
+  std::vector<void *> allocs;
+  std::string err;
+  long long h2d = 0, d2h = 0;
+  int launches = 0;
+  bool timing = false;
+  cudaEvent_t ev[32] = {};
+  int n_ev = 0;
+};
+
+namespace {
+
+mch_status set_err(mch_handle *h, mch_status s, const std::string &msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+mch_status cuda_fail(mch_handle *h, cudaError_t e, const char *where) {
+  return set_err(h, e == cudaErrorMemoryAllocation ? MCH_ERR_OOM : MCH_ERR_CUDA,
+                 std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call, where)                                  \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, where); \
+  } while (0)
+
+template <typename T>
+cudaError_t dalloc(mch_handle *h, T **p, size_t count) {
+  void *q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 16);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(q, 0, count * sizeof(T) + 16, h->st);
+  h->allocs.push_back(q);
+  *p = reinterpret_cast<T *>(q);
+  return e;
+}
+
+bool is_device_ptr(const void *p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Copies `bytes` between caller memory and library device memory in the given direction,
+// counting host traffic.
+cudaError_t stage(mch_handle *h, void *dst, const void *src, size_t bytes, bool to_device) {
+  if (to_device) {
+    const bool dev = is_device_ptr(src);
+    if (!dev) h->h2d += (long long)bytes;
+    return cudaMemcpyAsync(dst, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                           h->st);
+  }
+  const bool dev = is_device_ptr(dst);
+  if (!dev) h->d2h += (long long)bytes;
+  return cudaMemcpyAsync(dst, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                         h->st);
+}
+
+bool valid_level(const mch_handle *h, int level) {
+  return h && level >= 1 && level <= (int)h->lv.size();
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *mch_status_name(mch_status s) {
+  switch (s) {
+    case MCH_OK: return "MCH_OK";
+    case MCH_ERR_ARG: return "MCH_ERR_ARG";
+    case MCH_ERR_CUDA: return "MCH_ERR_CUDA";
+    case MCH_ERR_OOM: return "MCH_ERR_OOM";
+    case MCH_ERR_ORDER: return "MCH_ERR_ORDER";
+    case MCH_ERR_NOT_CONVERGED: return "MCH_ERR_NOT_CONVERGED";
+    case MCH_ERR_BREAKDOWN: return "MCH_ERR_BREAKDOWN";
+    case MCH_ERR_DEGENERATE: return "MCH_ERR_DEGENERATE";
+    case MCH_ERR_UNSUPPORTED: return "MCH_ERR_UNSUPPORTED";
+  }
+  return "MCH_UNKNOWN";
+}
+
+const char *mch_last_error(const mch_handle *h) { return h ? h->err.c_str() : "null handle"; }
+
+void mch_destroy(mch_handle *h) {
+  if (!h) return;
+  if (h->st) cudaStreamSynchronize(h->st);
+  else cudaDeviceSynchronize();
+  for (void *p : h->allocs) cudaFree(p);
+  for (int i = 0; i < h->n_ev; ++i) cudaEventDestroy(h->ev[i]);
+  delete h;
+}
+
+mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out) {
+  if (!out) return MCH_ERR_ARG;
+  *out = nullptr;
+  if (!desc) return MCH_ERR_ARG;
+  const mch_desc &d = *desc;
+  if (d.dim == 3) return MCH_ERR_UNSUPPORTED;
+  if (d.dim != 2 || d.n_cont < 1 || d.n_cont > MCH_MAX_CONT || d.n_levels < 1 || d.eta < 1 ||
+      d.macro_n < 1 || !d.level_stride || d.n_fine < 4 || d.periods < 1 || !(d.rve_len > 0) ||
+      (d.precision != MCH_FP64 && d.precision != MCH_MIXED) || d.rtol < 0 || d.inner_tol < 0 ||
+      d.max_iter < 0 || d.max_refine < 0)
+    return MCH_ERR_ARG;
+  if (d.overs != 0) return MCH_ERR_UNSUPPORTED;
+  const int nc = d.n_cont * d.periods * d.periods;
+  if (nc > MCH_MAX_NC) return MCH_ERR_UNSUPPORTED;
+
+  mch_handle *h = new mch_handle();
+  h->d = d;
+  h->strides.assign(d.level_stride, d.level_stride + d.n_levels);
+  h->d.level_stride = h->strides.data();
+  if (h->d.rtol == 0) h->d.rtol = 1e-8;
+  if (h->d.inner_tol == 0) h->d.inner_tol = 1e-4;
+  if (h->d.max_refine == 0) h->d.max_refine = 6;
+  h->st = (cudaStream_t)cuda_stream;
+  h->R = d.n_cont * (1 + d.dim);
+  h->nq = d.periods * d.periods;
+  h->nc = nc;
+  h->slots = 1 << d.dim;
+
+  std::vector<LevelPlan> plans;
+  std::string perr;
+  if (!build_plan(d.dim, d.macro_n, h->strides, d.n_fine, d.eta, plans, perr)) {
+    delete h;
+    return MCH_ERR_ARG;
+  }
+  // every level grid must be a supported power of two divisible by the coarsening
+  int scale = 1;
+  for (int l = 0; l < d.n_levels; ++l) {
+    if (d.n_fine % scale) { delete h; return MCH_ERR_ARG; }
+    const int n = d.n_fine / scale;
+    if (!pcg2d_supported(n, d.periods, d.precision == MCH_FP64)) {
+      delete h;
+      return MCH_ERR_UNSUPPORTED;
+    }
+    scale *= d.eta;
+  }
+
+  h->lv.resize(d.n_levels);
+  size_t max_unit_nv = 0, max_fine = 0, max_unit_nvc = 0;
+  const int nvf = nv_of(d.n_fine);
+  for (int l = 0; l < d.n_levels; ++l) {
+    Level &L = h->lv[l];
+    L.plan = plans[l];
+    L.n = L.plan.n_elem;
+    L.rho = d.n_fine / L.n;
+    L.npts = (int)L.plan.points.size() / d.dim;
+    L.nv = nv_of(L.n);
+    L.nvf = nvf;
+    max_unit_nv = std::max(max_unit_nv, (size_t)L.npts * h->R * L.nv);
+    max_unit_nvc = std::max(max_unit_nvc, (size_t)L.npts * h->R * L.nv);
+    if (l > 0) max_fine = std::max(max_fine, (size_t)L.npts * h->R * nvf);
+  }
+#define ALLOC(ptr, cnt)                                   \
+  do {                                                    \
+    cudaError_t e_ = dalloc(h, &(ptr), (size_t)(cnt));    \
+    if (e_ != cudaSuccess) {                              \
+      mch_destroy(h);                                     \
+      return e_ == cudaErrorMemoryAllocation ? MCH_ERR_OOM : MCH_ERR_CUDA; \
+    }                                                     \
+  } while (0)
+  for (int l = 0; l < d.n_levels; ++l) {
+    Level &L = h->lv[l];
+    const size_t np = L.npts, R = h->R, ne = (size_t)L.n * L.n;
+    ALLOC(L.kappa, np * ne);
+    ALLOC(L.labels, np * ne);
+    ALLOC(L.G, np * nc * R);
+    ALLOC(L.gI, np * nc * R);
+    ALLOC(L.Sinv64, np * nc * nc);
+    if (d.precision == MCH_MIXED) ALLOC(L.Sinv32, np * nc * nc);
+    ALLOC(L.x, np * R * L.nv);
+    if (l > 0) ALLOC(L.b, np * R * L.nv);
+    ALLOC(L.rho0, np * R);
+    ALLOC(L.ratio, np * R);
+    ALLOC(L.done, np * R);
+    ALLOC(L.iters, np * R);
+    ALLOC(L.ustat, np * R);
+    ALLOC(L.pstat, np);
+    ALLOC(L.dropped, np);
+    ALLOC(L.E, np * R * R);
+    ALLOC(L.phi, np * R * nvf);
+    if (l > 0) {
+      ALLOC(L.par_w, np * h->slots);
+      double **pp = nullptr;
+      ALLOC(pp, np * h->slots);
+      L.par_ptr = const_cast<const double **>(pp);
+      std::vector<const double *> hp(np * h->slots, nullptr);
+      for (size_t i = 0; i < np * h->slots; ++i) {
+        const int pl = L.plan.par_level[i];
+        if (pl > 0) hp[i] = h->lv[pl - 1].phi + (size_t)L.plan.par_pos[i] * R * nvf;
+      }
+      cudaError_t e = cudaMemcpyAsync(pp, hp.data(), hp.size() * sizeof(void *),
+                                      cudaMemcpyHostToDevice, h->st);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(L.par_w, L.plan.par_w.data(), L.plan.par_w.size() * sizeof(double),
+                            cudaMemcpyHostToDevice, h->st);
+      if (e != cudaSuccess) { mch_destroy(h); return MCH_ERR_CUDA; }
+    }
+  }
+  ALLOC(h->r64, max_unit_nv);
+  ALLOC(h->yc, max_unit_nvc);
+  if (max_fine) ALLOC(h->yfine, max_fine);
+  {
+    const size_t esz = d.precision == MCH_FP64 ? sizeof(double) : sizeof(float);
+    h->vec_bytes = max_unit_nv * esz;
+    char *v = nullptr;
+    ALLOC(v, h->vec_bytes);
+    h->vec = v;
+  }
+#undef ALLOC
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) { mch_destroy(h); return MCH_ERR_CUDA; }
+  *out = h;
+  return MCH_OK;
+}
+
+mch_status mch_plan_level(const mch_desc *desc, int level, int *n_points, int32_t *idx_out,
+                          int32_t *parent_level, int32_t *parent_pos, double *weight) {
+  if (!desc || !n_points || !desc->level_stride || level < 1 || level > desc->n_levels)
+    return MCH_ERR_ARG;
+  std::vector<int> strides(desc->level_stride, desc->level_stride + desc->n_levels);
+  std::vector<LevelPlan> plans;
+  std::string err;
+  if (desc->eta < 1 ||
+      !build_plan(desc->dim, desc->macro_n, strides, desc->n_fine, desc->eta, plans, err))
+    return MCH_ERR_ARG;
+  const LevelPlan &L = plans[level - 1];
+  *n_points = (int)L.points.size() / desc->dim;
+  if (idx_out)
+    for (size_t i = 0; i < L.points.size(); ++i) idx_out[i] = L.points[i];
+  for (size_t i = 0; i < L.par_level.size(); ++i) {
+    if (parent_level) parent_level[i] = L.par_level[i];
+    if (parent_pos) parent_pos[i] = L.par_pos[i];
+    if (weight) weight[i] = L.par_w[i];
+  }
+  return MCH_OK;
+}
+
+int mch_level_num_points(const mch_handle *h, int level) {
+  return valid_level(h, level) ? h->lv[level - 1].npts : -1;
+}
+
+int mch_level_n_elem(const mch_handle *h, int level) {
+  return valid_level(h, level) ? h->lv[level - 1].n : -1;
+}
+
+mch_status mch_level_points(const mch_handle *h, int level, int32_t *idx_out) {
+  if (!valid_level(h, level) || !idx_out) return MCH_ERR_ARG;
+  const auto &p = h->lv[level - 1].plan.points;
+  for (size_t i = 0; i < p.size(); ++i) idx_out[i] = p[i];
+  return MCH_OK;
+}
+
+mch_status mch_level_parents(const mch_handle *h, int level, int32_t *parent_level,
+                             int32_t *parent_pos, double *weight) {
+  if (!valid_level(h, level) || !parent_level || !parent_pos || !weight) return MCH_ERR_ARG;
+  const auto &L = h->lv[level - 1].plan;
+  for (size_t i = 0; i < L.par_level.size(); ++i) {
+    parent_level[i] = L.par_level[i];
+    parent_pos[i] = L.par_pos[i];
+    weight[i] = L.par_w[i];
+  }
+  return MCH_OK;
+}
+
+mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const uint8_t *labels) {
+  if (!valid_level(h, level) || !kappa || !labels) return set_err(h, MCH_ERR_ARG, "bad argument");
+  const int li = level - 1;
+  for (int k = 0; k < li; ++k)
+    if (!h->lv[k].solved)
+      return set_err(h, MCH_ERR_ORDER, "level " + std::to_string(level) +
+                                           " needs level " + std::to_string(k + 1) + " first");
+  Level &L = h->lv[li];
+  const mch_desc &d = h->d;
+  const int R = h->R, nc = h->nc, N = d.n_cont, P = d.periods;
+  const size_t np = L.npts, ne = (size_t)L.n * L.n;
+  const bool fp64 = d.precision == MCH_FP64;
+  cudaStream_t st = h->st;
+  h->h2d = h->d2h = 0;
+  h->launches = 0;
+  L.solved = false;
+
+  // phase marks for optional event timing: tag 0 setup, 1 interp, 2 pcg, 3 prep, 4 final
+  std::vector<int> tags;
+  const bool timing = h->timing && 3 + 2 * d.max_refine + 2 <= 32;
+  auto mark = [&](int tag) -> cudaError_t {
+    if (!timing) return cudaSuccess;
+    tags.push_back(tag);
+    return cudaEventRecord(h->ev[tags.size() - 1], st);
+  };
+  CK(stage(h, L.kappa, kappa, np * ne * sizeof(double), true), "stage kappa");
+  CK(stage(h, L.labels, labels, np * ne, true), "stage labels");
+
+  // ---- constraint data
+  SetupArgs sa{(int)np, L.n, P, N, R, nc, d.rve_len / L.n, d.rve_len, L.kappa, L.labels,
+               L.G, L.Sinv64, L.Sinv32, L.pstat, L.dropped};
+  CK(mark(-1), "event");
+  CK(launch_setup2d(sa, st), "setup");
+  ++h->launches;
+  CK(mark(0), "event");
+
+  const double inv_vol = 1.0 / (d.rve_len * d.rve_len);
+  const double *g = L.G;
+  const double *bvec = nullptr;
+  if (li > 0) {
+    // ---- interpolation and correction right-hand sides (level-1 grid, FP64)
+    CK(launch_interp((int)np, R, L.nvf, h->slots, L.par_ptr, L.par_w, L.phi, st), "interp");
+    ApplyArgs aa{(int)np, R, d.n_fine, L.rho, L.nvf, L.kappa, L.phi, nullptr, 0.0, h->yfine};
+    CK(launch_apply2d(aa, st), "apply fine");
+    CK(launch_gram((int)np, R, L.nvf, L.phi, h->yfine, inv_vol, 0.0, L.E, st), "gram I");
+    CK(launch_restrict2d((int)np, R, d.n_fine, L.rho, h->yfine, L.nvf, -1.0, L.b, L.nv, st),
+       "restrict");
+    const double s = 1.0 / ((double)L.rho * L.rho);
+    CK(launch_ctapply2d((int)np, R, d.n_fine, L.rho, P, N, nc, L.labels, L.phi, L.nvf, L.G, s,
+                        L.gI, st),
+       "ct fine");
+    h->launches += 5;
+    g = L.gI;
+    bvec = L.b;
+    CK(mark(1), "event");
+  }
+
+  // ---- constrained solves: FP64 refinement around PCG sweeps
+  CK(cudaMemsetAsync(L.x, 0, np * R * L.nv * sizeof(double), st), "zero x");
+  CK(cudaMemsetAsync(h->r64, 0, np * R * L.nv * sizeof(double), st), "zero r");
+  CK(cudaMemsetAsync(h->vec, 0, h->vec_bytes, st), "zero vec");
+  CK(cudaMemsetAsync(L.done, 0, np * R * sizeof(int), st), "zero done");
+  CK(cudaMemsetAsync(L.iters, 0, np * R * sizeof(int), st), "zero iters");
+  CK(cudaMemsetAsync(L.ustat, 0, np * R * sizeof(int), st), "zero status");
+  PrepArgs pa{(int)np, R, L.n, P, N, nc, L.nv, L.kappa, L.Sinv64, L.labels, g, bvec, L.x,
+              h->r64, h->vec, fp64 ? 1 : 0, 0, L.rho0, L.ratio, L.done, d.rtol};
+  CK(launch_prep2d(pa, st), "prep");
+  ++h->launches;
+  CK(mark(3), "event");
+  const int max_iter = d.max_iter > 0 ? d.max_iter : 4 * L.n + 50;
+  for (int sweep = 0; sweep < d.max_refine; ++sweep) {
+    if (fp64) {
+      PcgArgs<double> ga{(int)np, R, L.n, P, N, nc, L.nv, L.kappa, L.labels, L.Sinv64,
+                         reinterpret_cast<double *>(h->vec), L.done, L.iters, L.ustat,
+                         (float)d.inner_tol, max_iter};
+      CK(launch_pcg2d<double>(ga, st, &h->launches), "pcg fp64");
+    } else {
+      PcgArgs<float> ga{(int)np, R, L.n, P, N, nc, L.nv, L.kappa, L.labels, L.Sinv32,
+                        reinterpret_cast<float *>(h->vec), L.done, L.iters, L.ustat,
+                        (float)d.inner_tol, max_iter};
+      CK(launch_pcg2d<float>(ga, st, &h->launches), "pcg fp32");
+    }
+    CK(mark(2), "event");
+    pa.have_delta = 1;
+    CK(launch_prep2d(pa, st), "prep");
+    ++h->launches;
+    CK(mark(3), "event");
+  }
+
+  // ---- effective coefficients and the cell functions on the level-1 grid
+  ApplyArgs ac{(int)np, R, L.n, 1, L.nv, L.kappa, L.x, bvec, -2.0, h->yc};
+  CK(launch_apply2d(ac, st), "apply coarse");
+  CK(launch_gram((int)np, R, L.nv, L.x, h->yc, inv_vol, li > 0 ? 1.0 : 0.0, L.E, st), "gram");
+  h->launches += 2;
+  if (li == 0) {
+    CK(cudaMemcpyAsync(L.phi, L.x, np * R * L.nv * sizeof(double), cudaMemcpyDeviceToDevice, st),
+       "phi copy");
+  } else {
+    CK(launch_prolong_add2d((int)np, R, d.n_fine, L.rho, L.x, L.nv, L.phi, L.nvf, st), "prolong");
+    ++h->launches;
+  }
+  CK(mark(4), "event");
+
+  // ---- convergence record
+  std::vector<int> iters(np * R), ustat(np * R), pstat(np), dropped(np);
+  std::vector<double> ratio(np * R);
+  CK(cudaMemcpyAsync(iters.data(), L.iters, iters.size() * sizeof(int), cudaMemcpyDeviceToHost, st),
+     "read iters");
+  CK(cudaMemcpyAsync(ustat.data(), L.ustat, ustat.size() * sizeof(int), cudaMemcpyDeviceToHost, st),
+     "read status");
+  CK(cudaMemcpyAsync(pstat.data(), L.pstat, pstat.size() * sizeof(int), cudaMemcpyDeviceToHost, st),
+     "read pstat");
+  CK(cudaMemcpyAsync(dropped.data(), L.dropped, dropped.size() * sizeof(int),
+                     cudaMemcpyDeviceToHost, st),
+     "read dropped");
+  CK(cudaMemcpyAsync(ratio.data(), L.ratio, ratio.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                     st),
+     "read ratio");
+  CK(cudaStreamSynchronize(st), "level sync");
+
+  mch_level_stats &S = L.stats;
+  S = mch_level_stats{};
+  S.n_points = (int)np;
+  S.n_elem = L.n;
+  bool breakdown = false, degenerate = false, notconv = false;
+  int bad_pt = -1, bad_unit = -1;
+  for (size_t i = 0; i < np; ++i) {
+    S.n_dropped_rows += dropped[i];
+    if (pstat[i]) {
+      degenerate = true;
+      if (bad_pt < 0) bad_pt = (int)i;
+    }
+  }
+  for (size_t u = 0; u < np * R; ++u) {
+    S.total_iters += iters[u];
+    S.max_iters = std::max(S.max_iters, iters[u]);
+    const double rr = ratio[u];
+    if (!(rr == rr)) notconv = true;
+    else S.max_relres = std::max(S.max_relres, rr);
+    if (ustat[u] & 1) {
+      breakdown = true;
+      if (bad_unit < 0) bad_unit = (int)u;
+    }
+    if (!(rr < d.rtol)) notconv = true;
+  }
+  S.sweeps = d.max_refine;
+  S.pcg_launches = d.max_refine;
+  for (size_t u = 0; u < np * R; ++u)
+    S.pcg_node_iters += (long long)iters[u] * (long long)(L.n - 1) * (L.n - 1);
+  for (size_t k = 1; k < tags.size(); ++k) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, h->ev[k - 1], h->ev[k]), "event time");
+    switch (tags[k]) {
+      case 0: S.setup_ms += ms; break;
+      case 1: S.interp_ms += ms; break;
+      case 2: S.pcg_ms += ms; break;
+      case 3: S.prep_ms += ms; break;
+      case 4: S.final_ms += ms; break;
+    }
+  }
+  S.gpu_launches = h->launches;
+  S.h2d_bytes = h->h2d;
+  S.d2h_bytes = h->d2h;
+  if (degenerate)
+    return set_err(h, MCH_ERR_DEGENERATE,
+                   "point " + std::to_string(bad_pt) + " has flags " +
+                       std::to_string(pstat[bad_pt]) +
+                       " (1 kappa<=0, 2 label>=n_cont, 4 singular constraints, 8 absent continuum)");
+  L.solved = true;
+  if (breakdown)
+    return set_err(h, MCH_ERR_BREAKDOWN, "PCG breakdown at unit " + std::to_string(bad_unit));
+  if (notconv) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "largest residual ratio %.3e above rtol %.3e", S.max_relres, d.rtol);
+    return set_err(h, MCH_ERR_NOT_CONVERGED, buf);
+  }
+  h->err.clear();
+  return MCH_OK;
+}
+
+mch_status mch_effective_coeffs(mch_handle *h, int level, double *E, int32_t *iters,
+                                double *relres) {
+  if (!valid_level(h, level) || !E) return set_err(h, MCH_ERR_ARG, "bad argument");
+  Level &L = h->lv[level - 1];
+  if (!L.solved) return set_err(h, MCH_ERR_ORDER, "level not solved");
+  const size_t np = L.npts, R = h->R;
+  h->d2h = 0;
+  CK(stage(h, E, L.E, np * R * R * sizeof(double), false), "copy E");
+  if (iters) CK(stage(h, iters, L.iters, np * R * sizeof(int), false), "copy iters");
+  if (relres) CK(stage(h, relres, L.ratio, np * R * sizeof(double), false), "copy relres");
+  CK(cudaStreamSynchronize(h->st), "sync");
+  L.stats.d2h_bytes += h->d2h;
+  return MCH_OK;
+}
+
+mch_status mch_cell_functions(mch_handle *h, int level, double *phi) {
+  if (!valid_level(h, level) || !phi) return set_err(h, MCH_ERR_ARG, "bad argument");
+  Level &L = h->lv[level - 1];
+  if (!L.solved) return set_err(h, MCH_ERR_ORDER, "level not solved");
+  // library vectors are padded to nvf entries; the caller's layout is dense (n_fine+1)^2
+  const size_t row = (size_t)(h->d.n_fine + 1) * (h->d.n_fine + 1) * sizeof(double);
+  const size_t rows = (size_t)L.npts * h->R;
+  const bool dev = is_device_ptr(phi);
+  if (!dev) h->d2h += (long long)(row * rows);
+  CK(cudaMemcpy2DAsync(phi, row, L.phi, (size_t)L.nvf * sizeof(double), row, rows,
+                       dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st),
+     "copy phi");
+  CK(cudaStreamSynchronize(h->st), "sync");
+  return MCH_OK;
+}
+
+mch_status mch_set_timing(mch_handle *h, int enable) {
+  if (!h) return MCH_ERR_ARG;
+  if (enable && h->n_ev == 0) {
+    for (int i = 0; i < 32; ++i) {
+      if (cudaEventCreate(&h->ev[i]) != cudaSuccess) return set_err(h, MCH_ERR_CUDA, "event");
+      h->n_ev = i + 1;
+    }
+  }
+  h->timing = enable != 0;
+  return MCH_OK;
+}
+
+mch_status mch_level_stats_get(const mch_handle *h, int level, mch_level_stats *out) {
+  if (!valid_level(h, level) || !out) return MCH_ERR_ARG;
+  *out = h->lv[level - 1].stats;
+  out->n_points = h->lv[level - 1].npts;
+  out->n_elem = h->lv[level - 1].n;
+  return MCH_OK;
+}
+
+mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const *dL_dkappa) {
+  if (!h || !dL_dE || !dL_dkappa) return MCH_ERR_ARG;
+  return set_err(h, MCH_ERR_UNSUPPORTED, "backward pass not built yet");
+}
+
+}  // extern "C"

@@ -1,0 +1,138 @@
+// Shared device helpers for the 2D cell-problem kernels.
+//
+// Grid conventions (identical on every level): an RVE of n x n Q1 elements; element
+// (ex, ey) has flat index ex + n*ey; node vectors live on the padded (n+1) x (n+1)
+// lattice (node (kx, ky) at kx + (n+1)*ky), boundary entries are kept at zero, and each
+// vector of a batch starts at a multiple of `nv` = round_up((n+1)^2, 32) elements.
+//
+// Constraint rows (Sec. 2, Eqs. phi_avar and phi_grad): row b = j * P^2 + qy * P + qx for
+// continuum j and sub-block R_q = period (qx, qy). The library works with the row-scaled
+// operator Ct = (4 / h^2) C, whose entry for (row, node) is the number of elements of the
+// row's (continuum, sub-block) pair adjacent to the node; targets are scaled the same way.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#define MCH_MAX_CONT 4
+#define MCH_MAX_NC 64
+
+namespace mch {
+
+__host__ __device__ __forceinline__ int round_up(int a, int b) { return (a + b - 1) / b * b; }
+__host__ __device__ __forceinline__ int nv_of(int n) { return round_up((n + 1) * (n + 1), 32); }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Sum over aligned groups of `seg` lanes (seg a power of two <= 32).
+template <typename T>
+__device__ __forceinline__ T seg_sum(T v, int seg) {
+  for (int o = seg >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ void add_by_label(T (&acc)[MCH_MAX_CONT], int lab, T v) {
+#pragma unroll
+  for (int j = 0; j < MCH_MAX_CONT; ++j) acc[j] += (lab == j) ? v : T(0);
+}
+
+// Column-strip mapping used by every node kernel: lane c of a row of `n` threads owns node
+// column kx = c + 1 (active for c < n - 1) and row group G owns node rows
+// [1 + G*rpt, 1 + (G+1)*rpt). With rpt dividing m = n / P, the elements adjacent to a
+// thread's nodes lie in the thread's "main" sub-block (column c / m, row G*rpt / m) except
+// the east elements of lanes with (c+1) % m == 0 and the north elements of the strip's last
+// row when (G+1)*rpt is a multiple of m. Main-block contributions are accumulated per label
+// in registers; the others go straight to shared-memory bins.
+struct Strip {
+  int n, m, P, nq;
+  int c, kx;       // lane column, node column
+  int G, rpt;      // global row group, rows per thread
+  int bxm, bym;    // main sub-block
+  bool east_out;   // east elements belong to the next sub-block column
+  __device__ __forceinline__ void init(int n_, int P_, int lane_col, int row_group, int rpt_) {
+    n = n_;
+    P = P_;
+    m = n_ / P_;
+    nq = P_ * P_;
+    c = lane_col;
+    kx = lane_col + 1;
+    G = row_group;
+    rpt = rpt_;
+    bxm = c / m;
+    bym = (G * rpt) / m;
+    east_out = ((c + 1) % m) == 0;
+  }
+  __device__ __forceinline__ int bin(int lab, int ex, int ey) const {
+    return lab * nq + (ey / m) * P + (ex / m);
+  }
+};
+
+// Adds v (a node value) to the four constraint rows of the node's adjacent elements with
+// labels lSW, lSE, lNW, lNE; node row ky. Main-sub-block contributions go to acc[label],
+// the rest is added atomically to bins[].
+template <typename T>
+__device__ __forceinline__ void scatter_node(const Strip &s, int ky, int lSW, int lSE, int lNW,
+                                             int lNE, T v, T (&acc)[MCH_MAX_CONT], T *bins) {
+  const bool north_out = (ky / s.m) != s.bym;  // element row ky outside the main block row
+  // south elements (row ky-1) are always in the main block row
+  add_by_label(acc, lSW, v);
+  if (!s.east_out) add_by_label(acc, lSE, v);
+  else atomicAdd(&bins[s.bin(lSE, s.c + 1, ky - 1)], v);
+  if (!north_out) {
+    add_by_label(acc, lNW, v);
+    if (!s.east_out) add_by_label(acc, lNE, v);
+    else atomicAdd(&bins[s.bin(lNE, s.c + 1, ky)], v);
+  } else {
+    atomicAdd(&bins[s.bin(lNW, s.c, ky)], v);
+    atomicAdd(&bins[s.bin(lNE, s.c + 1, ky)], v);
+  }
+}
+
+// Reduces the per-label register accumulators over the lanes that share the main sub-block
+// (aligned groups of min(m, 32) lanes within a warp; callers guarantee the alignment) and
+// adds the group sums to bins[]. All 32 lanes of the warp must call it.
+template <typename T>
+__device__ __forceinline__ void flush_acc(const Strip &s, T (&acc)[MCH_MAX_CONT], int n_cont,
+                                          T *bins, bool lane_has_strip) {
+  const int seg = s.m < 32 ? s.m : 32;
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < MCH_MAX_CONT; ++j) {
+    if (j >= n_cont) break;
+    T v = seg_sum(acc[j], seg);
+    if ((lane & (seg - 1)) == 0 && lane_has_strip && v != T(0))
+      atomicAdd(&bins[j * s.nq + s.bym * s.P + s.bxm], v);
+  }
+}
+
+// Ct^T lambda at a node: sum of lambda over the rows of its four adjacent elements.
+template <typename T>
+__device__ __forceinline__ T ct_lambda(const Strip &s, int ky, int lSW, int lSE, int lNW, int lNE,
+                                       const T *lam) {
+  return lam[s.bin(lSW, s.c, ky - 1)] + lam[s.bin(lSE, s.c + 1, ky - 1)] +
+         lam[s.bin(lNW, s.c, ky)] + lam[s.bin(lNE, s.c + 1, ky)];
+}
+
+// 2D Q1 stencil at a node from the four adjacent kappas (a = SW, b = SE, c = NW, d = NE;
+// h^{d-2} = 1 in 2D) and the 3x3 neighbourhood of x. Element matrix entries 2/3 (same node),
+// -1/6 (edge neighbour), -1/3 (opposite corner).
+template <typename T>
+__device__ __forceinline__ T q1_apply(T a, T b, T c, T d, T xSW, T xS, T xSE, T xW, T x0, T xE,
+                                      T xNW, T xN, T xNE) {
+  const T t = T(4) * (a + b + c + d) * x0 - (b + d) * xE - (a + c) * xW - (c + d) * xN -
+              (a + b) * xS - T(2) * (d * xNE + c * xNW + b * xSE + a * xSW);
+  return t * T(1.0 / 6.0);
+}
+
+template <typename T>
+__device__ __forceinline__ T q1_diag(T a, T b, T c, T d) {
+  return (a + b + c + d) * T(2.0 / 3.0);
+}
+
+}  // namespace mch

@@ -1,0 +1,141 @@
+"""GPU parity: the sm_103a library through its C ABI against the FP64 oracle.
+
+Tolerances. A level's effective coefficients are stationary in its own cell functions
+(quadratic error) but depend linearly on its parents' functions, so the refinement
+tolerance rtol on the projected residual sets the accuracy of every child level. With
+rtol = 1e-11 both the FP64 mode and the mixed mode (FP32 PCG inside FP64 refinement) are
+asserted at a block-relative error of 1e-9 on every level; with the default rtol = 1e-8
+(the benchmark setting) the bound asserted is 1e-6.
+"""
+import numpy as np
+import pytest
+
+import mch_inputs as mi
+from oracle import cell, plan
+from util import block_rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2503_01276_gb300 as mch  # noqa: E402
+
+
+def _run_gpu(wl, levels=None, device=True, **kw):
+    s = mch.Solver.from_workload(wl, **kw)
+    out = []
+    L = wl.n_levels if levels is None else levels
+    for lev in range(1, L + 1):
+        pts = s.level_points(lev)
+        kap, lab = mi.media(wl, pts, s.n_elem(lev))
+        if device:
+            k_t = torch.from_numpy(kap).cuda()
+            l_t = torch.from_numpy(lab).cuda()
+            s.solve_level(lev, k_t, l_t)
+            E = torch.zeros((len(pts), s.R, s.R), dtype=torch.float64, device="cuda")
+            s.effective_coeffs(lev, E)
+            out.append(E.cpu().numpy())
+        else:
+            s.solve_level(lev, kap, lab)
+            out.append(s.effective_coeffs(lev))
+    return s, out
+
+
+def _run_oracle(wl):
+    pl = plan.level_plan(wl)
+    med = [mi.media(wl, l["points"], wl.n_level(k + 1)) for k, l in enumerate(pl)]
+    return cell.run_hierarchy(wl, pl, med)
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-9)])
+def test_level1_4x4_n32(precision, tol):
+    """2D, L = 1, 4x4 macropoints, 32x32 RVEs, two continua (full size of this workload)."""
+    wl = mi.workload("channel2d_4x4_n32", precision=precision)
+    s, Eg = _run_gpu(wl, rtol=1e-11)
+    Eo = _run_oracle(wl)
+    err = block_rel_err(Eg[0], Eo[0]["E"], wl.n_cont, wl.dim)
+    assert err < tol, err
+
+
+@pytest.mark.parametrize("name,n_fine,macro,strides", [
+    ("channel2d_17x17_L3", 64, 5, (4, 2, 1)),
+    ("channel2d_17x17_L3", 64, 9, (4, 2, 1)),
+    ("incl2d_33x33_L4", 128, 5, (4, 2, 1)),
+    ("channel2d_65x65_L3_adj", 64, 5, (2, 1)),
+])
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_hierarchy_small(name, n_fine, macro, strides, precision):
+    wl = mi.small_workload(name, n_fine=n_fine, macro_n=macro, strides=strides,
+                           precision=precision)
+    s, Eg = _run_gpu(wl, rtol=1e-11)
+    Eo = _run_oracle(wl)
+    for lev in range(wl.n_levels):
+        err = block_rel_err(Eg[lev], Eo[lev]["E"], wl.n_cont, wl.dim)
+        assert err < 1e-9, (lev + 1, err)
+    # the cell functions on the level-1 grid
+    for lev in range(1, wl.n_levels + 1):
+        phi = s.cell_functions(lev)
+        ref = Eo[lev - 1]["Phi"]
+        scale = np.abs(ref).max(axis=2, keepdims=True) + 1e-300
+        assert (np.abs(phi - ref) / scale).max() < 1e-9, lev
+
+
+def test_host_buffers_match_device_buffers():
+    """Host and device buffers give the same answer. Shared-memory reductions use atomics,
+    so two runs agree to the solver tolerance rather than bit for bit."""
+    wl = mi.small_workload("channel2d_17x17_L3", n_fine=32, macro_n=5, strides=(2, 1))
+    _, Ed = _run_gpu(wl, device=True, rtol=1e-11)
+    s, Eh = _run_gpu(wl, device=False, rtol=1e-11)
+    for a, b in zip(Ed, Eh):
+        assert block_rel_err(a, b, wl.n_cont, wl.dim) < 1e-10
+    st = s.stats(2)
+    assert st["h2d_bytes"] > 0
+
+
+def test_full_size_17x17_sampled():
+    """The benchmark workload (17x17 points, RVE grids 128/64/32, mixed precision) solved in
+    full on the GPU; sampled points of every level checked against the oracle, which
+    computes them (and their ancestors) one by one."""
+    wl = mi.workload("channel2d_17x17_L3")
+    s, Eg = _run_gpu(wl)
+    pl = plan.level_plan(wl)
+    targets = [(1, 0), (1, 4), (2, 0), (2, 37), (3, 0), (3, 101), (3, 207)]
+
+    def media_fn(lv, pos):
+        return mi.media(wl, pl[lv - 1]["points"][pos], wl.n_level(lv))
+
+    ref = cell.run_sampled(wl, pl, media_fn, targets)
+    for (lv, i) in targets:
+        err = block_rel_err(Eg[lv - 1][i], ref[(lv, i)]["E"], wl.n_cont, wl.dim)
+        assert err < 1e-6, (lv, i, err)
+    for lev in (1, 2, 3):
+        st = s.stats(lev)
+        assert st["max_relres"] < 1e-8
+
+
+def test_level_order_error():
+    wl = mi.small_workload("channel2d_17x17_L3", n_fine=32, macro_n=5, strides=(2, 1))
+    s = mch.Solver.from_workload(wl)
+    pts = s.level_points(2)
+    kap, lab = mi.media(wl, pts, s.n_elem(2))
+    with pytest.raises(mch.MchError) as e:
+        s.solve_level(2, kap, lab)
+    assert e.value.name == "MCH_ERR_ORDER"
+
+
+def test_invalid_medium_reported():
+    wl = mi.small_workload("channel2d_17x17_L3", n_fine=32, macro_n=3, strides=(1,))
+    s = mch.Solver.from_workload(wl)
+    pts = s.level_points(1)
+    kap, lab = mi.media(wl, pts, 32)
+    kap[1, 5] = -1.0
+    with pytest.raises(mch.MchError) as e:
+        s.solve_level(1, kap, lab)
+    assert e.value.name == "MCH_ERR_DEGENERATE"
+    kap, lab = mi.media(wl, pts, 32)
+    lab[:] = 1   # continuum 0 absent everywhere
+    with pytest.raises(mch.MchError) as e:
+        s.solve_level(1, kap, lab)
+    assert e.value.name == "MCH_ERR_DEGENERATE"
