@@ -32,7 +32,7 @@ struct Level {
   uint8_t *labels = nullptr;
   double *G = nullptr, *gI = nullptr, *Sinv64 = nullptr;
   float *Sinv32 = nullptr;
-  double *x = nullptr, *b = nullptr;
+  double *x = nullptr, *b = nullptr, *minv = nullptr;
   double *rho0 = nullptr, *ratio = nullptr;
   int *done = nullptr, *iters = nullptr, *ustat = nullptr, *pstat = nullptr, *dropped = nullptr;
   double *E = nullptr, *phi = nullptr;
@@ -114,6 +114,12 @@ cudaError_t stage(mch_handle *h, void *dst, const void *src, size_t bytes, bool 
   if (!dev) h->d2h += (long long)bytes;
   return cudaMemcpyAsync(dst, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                          h->st);
+}
+
+int ilog2(int v) {
+  int r = 0;
+  while ((1 << (r + 1)) <= v) ++r;
+  return r;
 }
 
 bool valid_level(const mch_handle *h, int level) {
@@ -229,6 +235,7 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
     ALLOC(L.Sinv64, np * nc * nc);
     if (d.precision == MCH_MIXED) ALLOC(L.Sinv32, np * nc * nc);
     ALLOC(L.x, np * R * L.nv);
+    ALLOC(L.minv, np * L.nv);
     if (l > 0) ALLOC(L.b, np * R * L.nv);
     ALLOC(L.rho0, np * R);
     ALLOC(L.ratio, np * R);
@@ -353,7 +360,7 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
 
   // ---- constraint data
   SetupArgs sa{(int)np, L.n, P, N, R, nc, d.rve_len / L.n, d.rve_len, L.kappa, L.labels,
-               L.G, L.Sinv64, L.Sinv32, L.pstat, L.dropped};
+               L.G, L.Sinv64, L.Sinv32, L.pstat, L.dropped, L.minv, L.nv};
   CK(mark(-1), "event");
   CK(launch_setup2d(sa, st), "setup");
   ++h->launches;
@@ -387,8 +394,9 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
   CK(cudaMemsetAsync(L.done, 0, np * R * sizeof(int), st), "zero done");
   CK(cudaMemsetAsync(L.iters, 0, np * R * sizeof(int), st), "zero iters");
   CK(cudaMemsetAsync(L.ustat, 0, np * R * sizeof(int), st), "zero status");
-  PrepArgs pa{(int)np, R, L.n, P, N, nc, L.nv, L.kappa, L.Sinv64, L.labels, g, bvec, L.x,
-              h->r64, h->vec, fp64 ? 1 : 0, 0, L.rho0, L.ratio, L.done, d.rtol};
+  PrepArgs pa{(int)np, R, L.n, P, N, nc, L.nv, L.kappa, L.Sinv64, L.minv, L.labels, g, bvec, L.x,
+              h->r64, h->vec, fp64 ? 1 : 0, 0, ilog2(L.n / P), ilog2(P), L.rho0, L.ratio,
+              L.done, d.rtol};
   CK(launch_prep2d(pa, st), "prep");
   ++h->launches;
   CK(mark(3), "event");
@@ -397,12 +405,12 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
     if (fp64) {
       PcgArgs<double> ga{(int)np, R, L.n, P, N, nc, L.nv, L.kappa, L.labels, L.Sinv64,
                          reinterpret_cast<double *>(h->vec), L.done, L.iters, L.ustat,
-                         (float)d.inner_tol, max_iter};
+                         (float)d.inner_tol, max_iter, ilog2(L.n / P), ilog2(P)};
       CK(launch_pcg2d<double>(ga, st, &h->launches), "pcg fp64");
     } else {
       PcgArgs<float> ga{(int)np, R, L.n, P, N, nc, L.nv, L.kappa, L.labels, L.Sinv32,
                         reinterpret_cast<float *>(h->vec), L.done, L.iters, L.ustat,
-                        (float)d.inner_tol, max_iter};
+                        (float)d.inner_tol, max_iter, ilog2(L.n / P), ilog2(P)};
       CK(launch_pcg2d<float>(ga, st, &h->launches), "pcg fp32");
     }
     CK(mark(2), "event");

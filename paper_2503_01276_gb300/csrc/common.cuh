@@ -50,26 +50,27 @@ __device__ __forceinline__ void add_by_label(T (&acc)[MCH_MAX_CONT], int lab, T 
 // row when (G+1)*rpt is a multiple of m. Main-block contributions are accumulated per label
 // in registers; the others go straight to shared-memory bins.
 struct Strip {
-  int n, m, P, nq;
+  int n, lgm, lgP, lgnq;
   int c, kx;       // lane column, node column
   int G, rpt;      // global row group, rows per thread
   int bxm, bym;    // main sub-block
   bool east_out;   // east elements belong to the next sub-block column
-  __device__ __forceinline__ void init(int n_, int P_, int lane_col, int row_group, int rpt_) {
+  __device__ __forceinline__ void init(int n_, int lgm_, int lgP_, int lane_col, int row_group,
+                                       int rpt_) {
     n = n_;
-    P = P_;
-    m = n_ / P_;
-    nq = P_ * P_;
+    lgm = lgm_;
+    lgP = lgP_;
+    lgnq = 2 * lgP_;
     c = lane_col;
     kx = lane_col + 1;
     G = row_group;
     rpt = rpt_;
-    bxm = c / m;
-    bym = (G * rpt) / m;
-    east_out = ((c + 1) % m) == 0;
+    bxm = c >> lgm;
+    bym = (G * rpt) >> lgm;
+    east_out = ((c + 1) & ((1 << lgm) - 1)) == 0;
   }
   __device__ __forceinline__ int bin(int lab, int ex, int ey) const {
-    return lab * nq + (ey / m) * P + (ex / m);
+    return (lab << lgnq) + ((ey >> lgm) << lgP) + (ex >> lgm);
   }
 };
 
@@ -79,7 +80,7 @@ struct Strip {
 template <typename T>
 __device__ __forceinline__ void scatter_node(const Strip &s, int ky, int lSW, int lSE, int lNW,
                                              int lNE, T v, T (&acc)[MCH_MAX_CONT], T *bins) {
-  const bool north_out = (ky / s.m) != s.bym;  // element row ky outside the main block row
+  const bool north_out = (ky >> s.lgm) != s.bym;  // element row ky outside the main block row
   // south elements (row ky-1) are always in the main block row
   add_by_label(acc, lSW, v);
   if (!s.east_out) add_by_label(acc, lSE, v);
@@ -100,14 +101,15 @@ __device__ __forceinline__ void scatter_node(const Strip &s, int ky, int lSW, in
 template <typename T>
 __device__ __forceinline__ void flush_acc(const Strip &s, T (&acc)[MCH_MAX_CONT], int n_cont,
                                           T *bins, bool lane_has_strip) {
-  const int seg = s.m < 32 ? s.m : 32;
+  const int m = 1 << s.lgm;
+  const int seg = m < 32 ? m : 32;
   const int lane = threadIdx.x & 31;
 #pragma unroll
   for (int j = 0; j < MCH_MAX_CONT; ++j) {
     if (j >= n_cont) break;
     T v = seg_sum(acc[j], seg);
     if ((lane & (seg - 1)) == 0 && lane_has_strip && v != T(0))
-      atomicAdd(&bins[j * s.nq + s.bym * s.P + s.bxm], v);
+      atomicAdd(&bins[(j << s.lgnq) + (s.bym << s.lgP) + s.bxm], v);
   }
 }
 

@@ -12,18 +12,13 @@ namespace {
 
 constexpr int PREP_THREADS = 512;
 
-__device__ __forceinline__ double node_minv(const double *kap, int n, int kx, int ky) {
-  const double s = kap[(kx - 1) + n * (ky - 1)] + kap[kx + n * (ky - 1)] +
-                   kap[(kx - 1) + n * ky] + kap[kx + n * ky];
-  return 1.0 / (s * (2.0 / 3.0));
-}
-
 // Accumulates Ct v over the CTA's node rows into bins (shared), one row at a time with a
 // flush whenever the next row leaves the current sub-block row. `val(kx, ky)` returns the
 // node value (called only for interior nodes of active lanes). Every thread of the CTA must
 // call it. n >= 16 lanes per row; rows are split into contiguous strips per row group.
 template <typename F>
-__device__ void ct_accumulate(int n, int P, int N, const uint8_t *lab, double *bins, F val) {
+__device__ void ct_accumulate(int n, int lgm, int lgP, int N, const uint8_t *lab, double *bins,
+                              F val) {
   const int tid = threadIdx.x;
   const int c = tid % n, g = tid / n;
   const int RG = PREP_THREADS / n;
@@ -31,10 +26,9 @@ __device__ void ct_accumulate(int n, int P, int N, const uint8_t *lab, double *b
   const bool col_active = c < n - 1;
   const int kx = c + 1;
   const int cE = c + 1 <= n - 1 ? c + 1 : n - 1;
-  const int m = n / P;
   double acc[MCH_MAX_CONT] = {0, 0, 0, 0};
   Strip s;
-  s.init(n, P, c, 1 + g * rpt - 1, 1);
+  s.init(n, lgm, lgP, c, g * rpt, 1);
   for (int i = 0; i < rpt; ++i) {
     const int ky = 1 + g * rpt + i;
     const bool act = col_active && ky <= n - 1;
@@ -45,11 +39,11 @@ __device__ void ct_accumulate(int n, int P, int N, const uint8_t *lab, double *b
     }
     const int kyn = ky + 1;
     const bool last = (i == rpt - 1);
-    if (last || ((kyn - 1) / m) != ((ky - 1) / m)) {
+    if (last || ((kyn - 1) >> lgm) != ((ky - 1) >> lgm)) {
       flush_acc(s, acc, N, bins, true);
 #pragma unroll
       for (int j = 0; j < MCH_MAX_CONT; ++j) acc[j] = 0.0;
-      s.init(n, P, c, kyn - 1, 1);
+      s.init(n, lgm, lgP, c, kyn - 1, 1);
     }
   }
 }
@@ -67,10 +61,11 @@ __device__ void for_own_nodes(int n, F f) {
   }
 }
 
-__device__ __forceinline__ double node_ct(const uint8_t *lab, int n, int P, int kx, int ky,
-                                          const double *lam) {
-  const int m = n / P, nq = P * P;
-  auto bin = [&](int ex, int ey) { return lab[ex + n * ey] * nq + (ey / m) * P + ex / m; };
+__device__ __forceinline__ double node_ct(const uint8_t *lab, int n, int lgm, int lgP, int kx,
+                                          int ky, const double *lam) {
+  auto bin = [&](int ex, int ey) {
+    return (lab[ex + n * ey] << (2 * lgP)) + ((ey >> lgm) << lgP) + (ex >> lgm);
+  };
   return lam[bin(kx - 1, ky - 1)] + lam[bin(kx, ky - 1)] + lam[bin(kx - 1, ky)] + lam[bin(kx, ky)];
 }
 
@@ -107,6 +102,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep2d(PrepArgs a) {
   double *r64 = a.r64 + (size_t)unit * a.nv;
   TI *vec = reinterpret_cast<TI *>(a.vec) + (size_t)unit * a.nv;
   const double *b = a.b ? a.b + (size_t)unit * a.nv : nullptr;
+  const double *mv = a.minv + (size_t)pt * a.nv;
   const int W = n + 1;
 
   __shared__ double bins[MCH_MAX_NC], gres[MCH_MAX_NC], mu[MCH_MAX_NC], red[PREP_THREADS / 32];
@@ -116,7 +112,7 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep2d(PrepArgs a) {
 
   // A. fold in the last correction, accumulate Ct x
   const bool hd = a.have_delta != 0;
-  ct_accumulate(n, P, N, lab, bins, [&](int kx, int ky) {
+  ct_accumulate(n, a.lgm, a.lgP, N, lab, bins, [&](int kx, int ky) {
     const int k = kx + W * ky;
     double v = x[k];
     if (hd) {
@@ -135,15 +131,15 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep2d(PrepArgs a) {
   // C. x += M^-1 Ct^T mu (restores Ct x = g)
   for_own_nodes(n, [&](int kx, int ky) {
     const int k = kx + W * ky;
-    x[k] += node_minv(kap, n, kx, ky) * node_ct(lab, n, P, kx, ky, mu);
+    x[k] += mv[k] * node_ct(lab, n, a.lgm, a.lgP, kx, ky, mu);
   });
   __syncthreads();
   // D. r = b - A x, accumulate Ct M^-1 r
-  ct_accumulate(n, P, N, lab, bins, [&](int kx, int ky) {
+  ct_accumulate(n, a.lgm, a.lgP, N, lab, bins, [&](int kx, int ky) {
     const int k = kx + W * ky;
     const double rr = (b ? b[k] : 0.0) - node_apply(kap, n, x, kx, ky);
     r64[k] = rr;
-    return node_minv(kap, n, kx, ky) * rr;
+    return mv[k] * rr;
   });
   __syncthreads();
   small_matvec(Si, bins, mu, nc);
@@ -152,8 +148,8 @@ __global__ void __launch_bounds__(PREP_THREADS) k_prep2d(PrepArgs a) {
   double rho = 0.0;
   for_own_nodes(n, [&](int kx, int ky) {
     const int k = kx + W * ky;
-    const double rt = r64[k] - node_ct(lab, n, P, kx, ky, mu);
-    rho += rt * rt * node_minv(kap, n, kx, ky);
+    const double rt = r64[k] - node_ct(lab, n, a.lgm, a.lgP, kx, ky, mu);
+    rho += rt * rt * mv[k];
     vec[k] = (TI)rt;
   });
   rho = warp_sum(rho);
@@ -206,14 +202,15 @@ __global__ void k_restrict2d(int R, int nf, int rho, const double *yf, int nvf, 
     return;
   }
   const double *y = yf + (size_t)unit * nvf;
+  const double ir = 1.0 / rho;  // exact: rho is a power of two
   double s = 0.0;
   for (int dy = -(rho - 1); dy <= rho - 1; ++dy) {
-    const double wy = 1.0 - fabs((double)dy) / rho;
+    const double wy = 1.0 - abs(dy) * ir;
     const int fy = Ky * rho + dy;
-    for (int dx = -(rho - 1); dx <= rho - 1; ++dx) {
-      const double wx = 1.0 - fabs((double)dx) / rho;
-      s += wx * wy * y[(Kx * rho + dx) + Wf * fy];
-    }
+    double sx = 0.0;
+    for (int dx = -(rho - 1); dx <= rho - 1; ++dx)
+      sx += (1.0 - abs(dx) * ir) * y[(Kx * rho + dx) + Wf * fy];
+    s += wy * sx;
   }
   o[k] = scale * s;
 }
@@ -225,7 +222,8 @@ __global__ void k_prolong_add2d(int nf, int rho, const double *xc, int nvc, doub
   if (k >= Wf * Wf) return;
   const int fx = k % Wf, fy = k / Wf;
   const int bx = min(fx / rho, ncg - 1), by = min(fy / rho, ncg - 1);
-  const double tx = (double)(fx - bx * rho) / rho, ty = (double)(fy - by * rho) / rho;
+  const double ir = 1.0 / rho;  // exact: rho is a power of two
+  const double tx = (fx - bx * rho) * ir, ty = (fy - by * rho) * ir;
   const double *x = xc + (size_t)unit * nvc;
   const double v = (1 - tx) * (1 - ty) * x[bx + Wc * by] + tx * (1 - ty) * x[bx + 1 + Wc * by] +
                    (1 - tx) * ty * x[bx + Wc * (by + 1)] + tx * ty * x[bx + 1 + Wc * (by + 1)];
@@ -248,8 +246,9 @@ __global__ void k_interp(int R, int nvf, int slots, const double *const *par_ptr
 
 // Fine-grid constraint functional with labels prolonged from the coarse grid.
 __global__ void __launch_bounds__(PREP_THREADS)
-    k_ctapply2d(int R, int nf, int rho, int P, int N, int nc, const uint8_t *labels_c,
-                const double *v, int nvf, const double *G, double s, double *g) {
+    k_ctapply2d(int R, int nf, int rho, int lgmf, int lgP, int N, int nc,
+                const uint8_t *labels_c, const double *v, int nvf, const double *G, double s,
+                double *g) {
   const int unit = blockIdx.x;
   const int pt = unit / R, r = unit % R;
   const int ncg = nf / rho;
@@ -276,21 +275,20 @@ __global__ void __launch_bounds__(PREP_THREADS)
     const int rpt = (n - 1 + RG - 1) / RG;
     const bool col_active = c < n - 1;
     const int kx = c + 1, cE = c + 1 <= n - 1 ? c + 1 : n - 1;
-    const int m = n / P;
     double acc[MCH_MAX_CONT] = {0, 0, 0, 0};
     Strip st;
-    st.init(n, P, c, gg * rpt, 1);
+    st.init(n, lgmf, lgP, c, gg * rpt, 1);
     for (int i = 0; i < rpt; ++i) {
       const int ky = 1 + gg * rpt + i;
       if (col_active && ky <= n - 1)
         scatter_node(st, ky, fl[c + n * (ky - 1)], fl[cE + n * (ky - 1)], fl[c + n * ky],
                      fl[cE + n * ky], vv[kx + (n + 1) * ky], acc, bins);
       const int kyn = ky + 1;
-      if (i == rpt - 1 || ((kyn - 1) / m) != ((ky - 1) / m)) {
+      if (i == rpt - 1 || ((kyn - 1) >> lgmf) != ((ky - 1) >> lgmf)) {
         flush_acc(st, acc, N, bins, true);
 #pragma unroll
         for (int j = 0; j < MCH_MAX_CONT; ++j) acc[j] = 0.0;
-        st.init(n, P, c, kyn - 1, 1);
+        st.init(n, lgmf, lgP, c, kyn - 1, 1);
       }
     }
   }
@@ -395,7 +393,11 @@ cudaError_t launch_interp(int npts, int R, int nvf, int slots, const double *con
 cudaError_t launch_ctapply2d(int npts, int R, int nf, int rho, int P, int N, int nc,
                              const uint8_t *labels_c, const double *v, int nvf,
                              const double *G, double s, double *g, cudaStream_t st) {
-  k_ctapply2d<<<npts * R, PREP_THREADS, 0, st>>>(R, nf, rho, P, N, nc, labels_c, v, nvf, G, s, g);
+  int lgP = 0, lgmf = 0;
+  while ((1 << (lgP + 1)) <= P) ++lgP;
+  while ((1 << (lgmf + 1)) <= nf / P) ++lgmf;
+  k_ctapply2d<<<npts * R, PREP_THREADS, 0, st>>>(R, nf, rho, lgmf, lgP, N, nc, labels_c, v, nvf,
+                                                  G, s, g);
   return cudaGetLastError();
 }
 

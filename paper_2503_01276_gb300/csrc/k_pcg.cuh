@@ -1,11 +1,12 @@
-// Shared-memory-resident projected PCG for the 2D constrained cell problems.
+// Shared-memory-resident projected PCG for the 2D constrained cell problems (template;
+// instantiated per precision in k_pcg_f32.cu and k_pcg_f64.cu).
 //
 // One (point, cell function) unit is one CTA, or one thread-block cluster of CL CTAs that
 // split the node rows into slabs and exchange halo rows and partial sums through
 // distributed shared memory. The unit's whole iteration state stays on chip for the sweep:
-// the search direction p and kappa in shared memory, x, r, A p and M^-1 in registers. HBM
-// is touched only to load kappa, labels, S^-1 and the initial residual, and to store the
-// correction at the end.
+// the search direction p, kappa and the labels in shared memory, x, r, A p and M^-1 in
+// registers. HBM is touched only to load kappa, labels, S^-1 and the initial residual, and
+// to store the correction at the end.
 //
 // Iteration (Sec. 3, Eq. phi_abstract: minimise the energy over the constraint set; the
 // method is projected conjugate gradients with the constraint preconditioner
@@ -16,19 +17,29 @@
 //   x += alpha p,  r <- r - alpha q - Ct^T lambda   (residual kept projected)
 //   rho' = r.z - 2 alpha z.q + alpha^2 q.M^-1 q - lambda.c     (= new r.M^-1 r)
 //   p = M^-1 r + (rho'/rho) p
-// so every iteration has a single reduction phase. Keeping r projected (rather than
+// so every iteration has one reduction phase and two barriers (p visible, partial sums
+// complete). Every warp evaluates the scalars and lambda from the reduced sums itself, so
+// no warp waits on another after the reduction. Keeping r projected (rather than
 // projecting only z) avoids the cancellation that otherwise pushes FP32 iterates off the
 // constraint set.
+//
+// Constraint rows: node k contributes v_k to the row of each of its four adjacent elements.
+// A thread's column strip has fixed west/east element columns, so the west and east
+// contributions are accumulated per label in registers (static slots); the east slot of
+// lane c belongs to column c+1, whose owner is lane c+1, and is handed over with one
+// shfl_up. Rows per thread divide the sub-block size, so all south elements of a strip lie
+// in one sub-block row; only the north elements of the strip's last row can fall in the
+// next one, and those few go straight to shared-memory atomics.
+#pragma once
+
 #include <cooperative_groups.h>
 
 #include "common.cuh"
 #include "kernels.h"
 
-namespace cg = cooperative_groups;
-
 namespace mch {
 
-namespace {
+namespace cg = cooperative_groups;
 
 template <typename T, int CL>
 struct ClusterOps {
@@ -46,13 +57,17 @@ struct ClusterOps {
   }
 };
 
-template <typename T>
-__device__ __forceinline__ T rcp(T v) { return T(1) / v; }
+template <int NC, typename T>
+__device__ __forceinline__ void add_lab(T (&acc)[NC], int lab, T v) {
+#pragma unroll
+  for (int j = 0; j < NC; ++j) acc[j] += (lab == j) ? v : T(0);
+}
 
-template <typename T, int NEL, int RG, int RPT, int CL>
+template <typename T, int NEL, int RG, int RPT, int CL, int NC>
 __global__ void __launch_bounds__(NEL * RG) k_pcg2d(PcgArgs<T> a) {
   using C = ClusterOps<T, CL>;
   constexpr int THREADS = NEL * RG;
+  constexpr int NWARPS = THREADS / 32;
   constexpr int ROWS = RG * RPT;
   constexpr int W = NEL + 1;
   const int n = NEL;
@@ -62,15 +77,17 @@ __global__ void __launch_bounds__(NEL * RG) k_pcg2d(PcgArgs<T> a) {
   const int pt = unit / a.R;
   const int nc = a.nc;
   const int NRED = 4 + 2 * nc;
+  const int lgm = a.lgm, lgP = a.lgP, lgnq = 2 * a.lgP;
+  const int m = 1 << lgm;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T *ps = reinterpret_cast<T *>(smem_raw);   // [(ROWS+2)][W] search direction with halo rows
   T *ks = ps + (ROWS + 2) * W;               // [(ROWS+1)][NEL] kappa of element rows r_lo-1..
-  T *sinv = ks + (ROWS + 1) * NEL;           // [nc][nc]
+  T *sinv = ks + (ROWS + 1) * NEL;           // [nc][nc] (symmetric)
   T *red = sinv + nc * nc;                   // [2][NRED] partial sums (double-buffered)
-  T *lam = red + 2 * NRED;                   // [nc]
-  T *tot = lam + nc;                         // [NRED]
-  T *bc = tot + NRED;                        // [8] broadcast scalars
+  T *twarp = red + 2 * NRED;                 // [NWARPS][NRED] per-warp totals
+  T *lamw = twarp + NWARPS * NRED;           // [NWARPS][nc] per-warp multipliers
+  T *bc = lamw + NWARPS * nc;                // [8]
   uint8_t *ls = reinterpret_cast<uint8_t *>(bc + 8);  // [(ROWS+1)][NEL] labels
 
   const int tid = threadIdx.x;
@@ -78,12 +95,16 @@ __global__ void __launch_bounds__(NEL * RG) k_pcg2d(PcgArgs<T> a) {
   const int c = tid % NEL, g = tid / NEL;
   const int G = rank * RG + g;
   const int r_lo = 1 + rank * ROWS;
-  Strip s;
-  s.init(n, a.P, c, G, RPT);
   const int kx = c + 1;
   const int kxE = kx + 1 <= n ? kx + 1 : n;   // clamp for the inactive last lane
   const int cE = c + 1 <= n - 1 ? c + 1 : n - 1;
   const bool col_active = c < n - 1;
+  const int bxW = c >> lgm, bxE = cE >> lgm;
+  const int bym = (G * RPT) >> lgm;
+  // north elements of the strip's last row lie in the next sub-block row
+  const bool next_row = (((G + 1) * RPT) & (m - 1)) == 0;
+  const int baseW = (bym << lgP) + bxW, baseE = (bym << lgP) + bxE;
+  const int baseWn = ((bym + 1) << lgP) + bxW, baseEn = ((bym + 1) << lgP) + bxE;
 
   // ---- load the unit's data
   const double *kap = a.kappa + (size_t)pt * n * n;
@@ -113,29 +134,25 @@ __global__ void __launch_bounds__(NEL * RG) k_pcg2d(PcgArgs<T> a) {
     rr[i] = act ? vec[kx + (n + 1) * ky] : T(0);
     const T dg = q1_diag(ks[(lr - 1) * NEL + c], ks[(lr - 1) * NEL + cE], ks[lr * NEL + c],
                          ks[lr * NEL + cE]);
-    mi[i] = act ? rcp(dg) : T(0);
+    mi[i] = act ? T(1) / dg : T(0);
     const T z = mi[i] * rr[i];
     dz += rr[i] * z;
     if (act) ps[lr * W + kx] = z;
   }
-  // halo push of the initial direction
   if constexpr (CL > 1) {
     if (g == 0 && rank > 0) C::remote(ps, rank - 1)[(ROWS + 1) * W + kx] = ps[1 * W + kx];
     if (g == RG - 1 && rank < CL - 1) C::remote(ps, rank + 1)[kx] = ps[ROWS * W + kx];
   }
   dz = warp_sum(dz);
-  if (lane == 0) atomicAdd(&red[NRED + 0], dz);   // initial phase uses buffer 1
+  if (lane == 0) atomicAdd(&red[NRED + 0], dz);   // the initial phase uses buffer 1
   C::sync();
-  if (warp == 0) {
-    T v = T(0);
-    for (int rk = 0; rk < CL; ++rk) v += C::remote(red, rk)[NRED + 0];
-    if (lane == 0) bc[4] = v;
-  }
-  __syncthreads();
-  const T rho0 = bc[4];
+  T rho0 = T(0);
+  for (int rk = 0; rk < CL; ++rk) rho0 += C::remote(red, rk)[NRED + 0];
   T rho = rho0;
   int it = 0;
   bool breakdown = false;
+  T *tw = twarp + warp * NRED;
+  T *lw = lamw + warp * nc;
 
   if (rho0 > T(0)) {
     for (;; ++it) {
@@ -146,7 +163,9 @@ __global__ void __launch_bounds__(NEL * RG) k_pcg2d(PcgArgs<T> a) {
 
       // ---- q = A p with a sliding 3-row window, plus the partial sums
       T pq = 0, zq = 0, qmq = 0, rz = 0;
-      T accz[MCH_MAX_CONT] = {0, 0, 0, 0}, accq[MCH_MAX_CONT] = {0, 0, 0, 0};
+      T azW[NC], azE[NC], aqW[NC], aqE[NC];
+#pragma unroll
+      for (int j = 0; j < NC; ++j) azW[j] = azE[j] = aqW[j] = aqE[j] = T(0);
       int lr = 1 + g * RPT;
       T pW0 = ps[(lr - 1) * W + kx - 1], pC0 = ps[(lr - 1) * W + kx], pE0 = ps[(lr - 1) * W + kxE];
       T pW1 = ps[lr * W + kx - 1], pC1 = ps[lr * W + kx], pE1 = ps[lr * W + kxE];
@@ -169,13 +188,46 @@ __global__ void __launch_bounds__(NEL * RG) k_pcg2d(PcgArgs<T> a) {
         zq += z * qv;
         qmq += qv * mq;
         rz += rr[i] * z;
-        if (act) {
-          scatter_node(s, ky, lS0, lS1, lN0, lN1, z, accz, rb + 4);
-          scatter_node(s, ky, lS0, lS1, lN0, lN1, mq, accq, rb + 4 + nc);
+        // inactive nodes carry z = mq = 0, so their contributions vanish
+        add_lab<NC>(azW, lS0, z);
+        add_lab<NC>(azE, lS1, z);
+        add_lab<NC>(aqW, lS0, mq);
+        add_lab<NC>(aqE, lS1, mq);
+        if (i < RPT - 1 || !next_row) {
+          add_lab<NC>(azW, lN0, z);
+          add_lab<NC>(azE, lN1, z);
+          add_lab<NC>(aqW, lN0, mq);
+          add_lab<NC>(aqE, lN1, mq);
+        } else if (act) {
+          atomicAdd(&rb[4 + (lN0 << lgnq) + baseWn], z);
+          atomicAdd(&rb[4 + (lN1 << lgnq) + baseEn], z);
+          atomicAdd(&rb[4 + nc + (lN0 << lgnq) + baseWn], mq);
+          atomicAdd(&rb[4 + nc + (lN1 << lgnq) + baseEn], mq);
         }
         pW0 = pW1; pC0 = pC1; pE0 = pE1;
         pW1 = pW2; pC1 = pC2; pE1 = pE2;
         kS0 = kN0; kS1 = kN1; lS0 = lN0; lS1 = lN1;
+      }
+      // hand the east slots to the owner of column c+1; lane 31 hands over through shared
+      const int seg = m < 32 ? m : 32;
+#pragma unroll
+      for (int j = 0; j < NC; ++j) {
+        const T uz = __shfl_up_sync(0xffffffffu, azE[j], 1);
+        const T uq = __shfl_up_sync(0xffffffffu, aqE[j], 1);
+        if (lane > 0) {  // lane 0's west column gets the east slot of the previous warp's
+          azW[j] += uz;  // lane 31, which adds it to shared memory itself
+          aqW[j] += uq;
+        }
+        if (lane == 31 && (azE[j] != T(0) || aqE[j] != T(0))) {
+          atomicAdd(&rb[4 + (j << lgnq) + baseE], azE[j]);
+          atomicAdd(&rb[4 + nc + (j << lgnq) + baseE], aqE[j]);
+        }
+        const T sz = seg_sum(azW[j], seg);
+        const T sq = seg_sum(aqW[j], seg);
+        if ((lane & (seg - 1)) == 0) {
+          atomicAdd(&rb[4 + (j << lgnq) + baseW], sz);
+          atomicAdd(&rb[4 + nc + (j << lgnq) + baseW], sq);
+        }
       }
       pq = warp_sum(pq);
       zq = warp_sum(zq);
@@ -187,63 +239,68 @@ __global__ void __launch_bounds__(NEL * RG) k_pcg2d(PcgArgs<T> a) {
         atomicAdd(&rb[2], qmq);
         atomicAdd(&rb[3], rz);
       }
-      flush_acc(s, accz, a.N, rb + 4, true);
-      flush_acc(s, accq, a.N, rb + 4 + nc, true);
       C::sync();  // B2: every partial of every CTA is in place
 
-      // ---- scalars and multipliers (warp 0 of each CTA, identical on every rank)
-      if (warp == 0) {
-        for (int t = lane; t < NRED; t += 32) {
-          T v = T(0);
-          for (int rk = 0; rk < CL; ++rk) v += C::remote(rb, rk)[t];
-          tot[t] = v;
-        }
-        __syncwarp();
-        const T tpq = tot[0], tzq = tot[1], tqmq = tot[2], trz = tot[3];
-        T alpha = rho / tpq;
-        const bool bad = !(tpq > T(0)) || !(alpha == alpha) || !(alpha < T(3.0e38));
-        if (bad) alpha = T(0);
-        for (int t = lane; t < nc; t += 32) tot[4 + t] = tot[4 + t] - alpha * tot[4 + nc + t];
-        __syncwarp();
-        T lc = T(0);
-        for (int i = lane; i < nc; i += 32) {
-          T l = T(0);
-          for (int j = 0; j < nc; ++j) l += sinv[i * nc + j] * tot[4 + j];
-          lam[i] = bad ? T(0) : l;
-          lc += l * tot[4 + i];
-        }
-        lc = warp_sum(lc);
-        const T rho_new = trz - T(2) * alpha * tzq + alpha * alpha * tqmq - lc;
-        if (lane == 0) {
-          int stop = 0;
-          if (bad) stop = 2;
-          else if (!(rho_new > a.tol * a.tol * rho0)) stop = 1;
-          else if (it + 1 >= a.max_iter) stop = 1;
-          bc[0] = alpha;
-          bc[1] = stop ? T(0) : rho_new / rho;
-          bc[2] = T(stop);
-          bc[3] = rho_new;
-        }
+      // ---- scalars and multipliers, evaluated by every warp from the same sums
+      for (int t = lane; t < NRED; t += 32) {
+        T v = T(0);
+        for (int rk = 0; rk < CL; ++rk) v += C::remote(rb, rk)[t];
+        tw[t] = v;
       }
-      __syncthreads();  // B3
-      const T alpha = bc[0], beta = bc[1];
-      const int stop = (int)bc[2];
-      rho = bc[3];
+      __syncwarp();
+      const T tpq = tw[0], tzq = tw[1], tqmq = tw[2], trz = tw[3];
+      T alpha = rho / tpq;
+      const bool bad = !(tpq > T(0)) || !(alpha == alpha) || !(alpha < T(3.0e38));
+      if (bad) alpha = T(0);
+      __syncwarp();
+      for (int t = lane; t < nc; t += 32) tw[4 + t] = tw[4 + t] - alpha * tw[4 + nc + t];
+      __syncwarp();
+      T lc = T(0);
+      for (int i = lane; i < nc; i += 32) {
+        // S^-1 is symmetric: column i is read so that consecutive lanes hit distinct banks
+        T l0 = T(0), l1 = T(0), l2 = T(0), l3 = T(0);
+        int j = 0;
+        for (; j + 3 < nc; j += 4) {
+          l0 += sinv[(j + 0) * nc + i] * tw[4 + j + 0];
+          l1 += sinv[(j + 1) * nc + i] * tw[4 + j + 1];
+          l2 += sinv[(j + 2) * nc + i] * tw[4 + j + 2];
+          l3 += sinv[(j + 3) * nc + i] * tw[4 + j + 3];
+        }
+        for (; j < nc; ++j) l0 += sinv[j * nc + i] * tw[4 + j];
+        const T l = (l0 + l1) + (l2 + l3);
+        lw[i] = bad ? T(0) : l;
+        lc += l * tw[4 + i];
+      }
+      lc = warp_sum(lc);
+      __syncwarp();
+      const T rho_new = trz - T(2) * alpha * tzq + alpha * alpha * tqmq - lc;
+      int stop = 0;
+      if (bad) stop = 2;
+      else if (!(rho_new > T(a.tol) * T(a.tol) * rho0)) stop = 1;
+      else if (it + 1 >= a.max_iter) stop = 1;
+      const T beta = stop ? T(0) : rho_new / rho;
+      rho = rho_new;
 
-      // ---- updates
+      // ---- updates (labels again through a sliding window)
+      lr = 1 + g * RPT;
+      lS0 = ls[(lr - 1) * NEL + c];
+      lS1 = ls[(lr - 1) * NEL + cE];
 #pragma unroll
-      for (int i = 0; i < RPT; ++i) {
-        const int lrr = 1 + g * RPT + i;
-        const int ky = r_lo + lrr - 1;
+      for (int i = 0; i < RPT; ++i, ++lr) {
+        const int lN0 = ls[lr * NEL + c], lN1 = ls[lr * NEL + cE];
+        const int ky = r_lo + lr - 1;
         const bool act = col_active && ky <= n - 1;
-        if (!act) continue;
-        const T p0 = ps[lrr * W + kx];
+        const bool nr = (i == RPT - 1) && next_row && act;  // keeps inactive bins in range
+        const T p0 = ps[lr * W + kx];
         x[i] += alpha * p0;
-        const T cl = ct_lambda(s, ky, ls[(lrr - 1) * NEL + c], ls[(lrr - 1) * NEL + cE],
-                               ls[lrr * NEL + c], ls[lrr * NEL + cE], lam);
-        rr[i] = rr[i] - alpha * q[i] - cl;
+        const T cl = lw[(lS0 << lgnq) + baseW] + lw[(lS1 << lgnq) + baseE] +
+                     lw[(lN0 << lgnq) + (nr ? baseWn : baseW)] +
+                     lw[(lN1 << lgnq) + (nr ? baseEn : baseE)];
+        rr[i] = act ? rr[i] - alpha * q[i] - cl : T(0);
         const T pn = mi[i] * rr[i] + beta * p0;
-        if (!stop) ps[lrr * W + kx] = pn;
+        if (act && !stop) ps[lr * W + kx] = pn;
+        lS0 = lN0;
+        lS1 = lN1;
       }
       if (stop) {
         breakdown = (stop == 2);
@@ -270,15 +327,15 @@ __global__ void __launch_bounds__(NEL * RG) k_pcg2d(PcgArgs<T> a) {
   C::sync();  // no CTA leaves while a peer may still read its shared memory
 }
 
-template <typename T, int NEL, int RG, int RPT, int CL>
-cudaError_t launch_cfg(const PcgArgs<T> &a, cudaStream_t st) {
+template <typename T, int NEL, int RG, int RPT, int CL, int NC>
+cudaError_t launch_pcg_cfg(const PcgArgs<T> &a, cudaStream_t st) {
   constexpr int THREADS = NEL * RG;
   constexpr int ROWS = RG * RPT;
   const int nred = 4 + 2 * a.nc;
   const size_t smem = sizeof(T) * ((ROWS + 2) * (NEL + 1) + (ROWS + 1) * NEL + a.nc * a.nc +
-                                   2 * nred + a.nc + nred + 8) +
+                                   2 * nred + (THREADS / 32) * (nred + a.nc) + 8) +
                       (ROWS + 1) * NEL + 16;
-  auto kern = k_pcg2d<T, NEL, RG, RPT, CL>;
+  auto kern = k_pcg2d<T, NEL, RG, RPT, CL, NC>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -292,53 +349,17 @@ cudaError_t launch_cfg(const PcgArgs<T> &a, cudaStream_t st) {
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = CL > 1 ? 1 : 0;
   e = cudaLaunchKernelEx(&cfg, kern, a);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
-}  // namespace
-
-bool pcg2d_supported(int n, int P, bool fp64) {
-  if (P < 1 || n % P) return false;
-  const int m = n / P;
-  if (m < 2 || (m & (m - 1))) return false;
-  int rpt;
-  switch (n) {
-    case 16: rpt = 1; break;
-    case 32: rpt = 4; break;
-    case 64: rpt = fp64 ? 4 : 8; break;
-    case 128: rpt = fp64 ? 8 : 16; break;
-    case 256: if (fp64) return false; rpt = 16; break;
-    default: return false;
-  }
-  return m % rpt == 0;
-}
-
-template <>
-cudaError_t launch_pcg2d<float>(const PcgArgs<float> &a, cudaStream_t st, int *launches) {
-  if (launches) ++*launches;
-  switch (a.n) {
-    case 16: return launch_cfg<float, 16, 16, 1, 1>(a, st);
-    case 32: return launch_cfg<float, 32, 8, 4, 1>(a, st);
-    case 64: return launch_cfg<float, 64, 8, 8, 1>(a, st);
-    case 128: return launch_cfg<float, 128, 4, 16, 2>(a, st);
-    case 256: return launch_cfg<float, 256, 2, 16, 8>(a, st);
-  }
-  return cudaErrorInvalidValue;
-}
-
-template <>
-cudaError_t launch_pcg2d<double>(const PcgArgs<double> &a, cudaStream_t st, int *launches) {
-  if (launches) ++*launches;
-  switch (a.n) {
-    case 16: return launch_cfg<double, 16, 16, 1, 1>(a, st);
-    case 32: return launch_cfg<double, 32, 8, 4, 1>(a, st);
-    case 64: return launch_cfg<double, 64, 8, 4, 2>(a, st);
-    case 128: return launch_cfg<double, 128, 4, 8, 4>(a, st);
-  }
-  return cudaErrorInvalidValue;
+template <typename T, int NEL, int RG, int RPT, int CL>
+cudaError_t launch_pcg_nc(const PcgArgs<T> &a, cudaStream_t st) {
+  if (a.N <= 2) return launch_pcg_cfg<T, NEL, RG, RPT, CL, 2>(a, st);
+  if (a.N == 3) return launch_pcg_cfg<T, NEL, RG, RPT, CL, 3>(a, st);
+  return launch_pcg_cfg<T, NEL, RG, RPT, CL, 4>(a, st);
 }
 
 }  // namespace mch

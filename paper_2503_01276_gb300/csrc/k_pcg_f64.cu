@@ -1,0 +1,34 @@
+// FP64 instantiations of the shared-memory PCG sweep (the plain FP64 mode).
+#include "k_pcg.cuh"
+
+namespace mch {
+
+bool pcg2d_supported(int n, int P, bool fp64) {
+  if (P < 1 || (P & (P - 1)) || n % P) return false;
+  const int m = n / P;
+  if (m < 2 || (m & (m - 1))) return false;
+  int rpt;  // rows per thread of the launch shape used for this n (k_pcg_f32.cu / below)
+  switch (n) {
+    case 16: rpt = 1; break;
+    case 32: rpt = 4; break;
+    case 64: rpt = 4; break;
+    case 128: rpt = 8; break;
+    case 256: if (fp64) return false; rpt = 16; break;
+    default: return false;
+  }
+  return m % rpt == 0;
+}
+
+template <>
+cudaError_t launch_pcg2d<double>(const PcgArgs<double> &a, cudaStream_t st, int *launches) {
+  if (launches) ++*launches;
+  switch (a.n) {
+    case 16: return launch_pcg_nc<double, 16, 16, 1, 1>(a, st);
+    case 32: return launch_pcg_nc<double, 32, 8, 4, 1>(a, st);
+    case 64: return launch_pcg_nc<double, 64, 8, 4, 2>(a, st);
+    case 128: return launch_pcg_nc<double, 128, 4, 8, 4>(a, st);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace mch

@@ -108,6 +108,20 @@ __global__ void __launch_bounds__(SETUP_THREADS) k_setup2d(SetupArgs a) {
     G[t] = v;
   }
 
+  // M^-1 = 1 / diag(A) at interior nodes, kept for the FP64 refinement steps
+  {
+    double *mv = a.minv + (size_t)pt * a.nv;
+    const int W = n + 1;
+    for (int k = tid; k < W * W; k += SETUP_THREADS) {
+      const int kx = k % W, ky = k / W;
+      double v = 0.0;
+      if (kx > 0 && ky > 0 && kx < n && ky < n)
+        v = 1.0 / ((kap[(kx - 1) + n * (ky - 1)] + kap[kx + n * (ky - 1)] + kap[(kx - 1) + n * ky] +
+                    kap[kx + n * ky]) * (2.0 / 3.0));
+      mv[k] = v;
+    }
+  }
+
   // 5. S = Ct M^-1 Ct^T: per node, sum over pairs of adjacent elements of 1/diag; runs of
   // nodes with the same four adjacent rows are accumulated before the atomic flush.
   {

@@ -16,6 +16,8 @@ struct SetupArgs {
   float *Sinv32;          // [pt][nc][nc] or null
   int *status;            // [pt] bit0 kappa, bit1 label, bit2 singular S, bit3 absent continuum
   int *dropped;           // [pt]
+  double *minv;           // [pt][nv] 1 / diag(A) at interior nodes (0 elsewhere)
+  int nv;
 };
 cudaError_t launch_setup2d(const SetupArgs &a, cudaStream_t st);
 
@@ -34,6 +36,7 @@ struct PcgArgs {
   int *status;            // [pt*R] |= 1 on breakdown
   float tol;              // stop when sqrt(rho / rho0) < tol
   int max_iter;
+  int lgm, lgP;           // log2(n / P), log2(P)
 };
 template <typename T>
 cudaError_t launch_pcg2d(const PcgArgs<T> &a, cudaStream_t st, int *launches);
@@ -46,7 +49,7 @@ bool pcg2d_supported(int n, int P, bool fp64);
 // next PCG sweep (as T_inner) unless converged.
 struct PrepArgs {
   int npts, R, n, P, N, nc, nv;
-  const double *kappa, *Sinv64;
+  const double *kappa, *Sinv64, *minv;
   const uint8_t *labels;
   const double *g;        // [pt][nc][R] scaled targets of this level's problem
   const double *b;        // [pt][R][nv] right-hand side (null = 0)
@@ -55,6 +58,7 @@ struct PrepArgs {
   void *vec;              // [pt][R][nv] inner vector (float or double): in delta, out residual
   int inner_fp64;
   int have_delta;
+  int lgm, lgP;           // log2(n / P), log2(P)
   double *rho0;           // [pt*R]
   double *ratio;          // [pt*R]
   int *done;              // [pt*R]
