@@ -33,8 +33,8 @@ struct Level {
   double *G = nullptr, *gI = nullptr, *Sinv64 = nullptr;
   float *Sinv32 = nullptr;
   double *x = nullptr, *b = nullptr, *minv = nullptr;
-  double *rho0 = nullptr, *ratio = nullptr;
-  int *done = nullptr, *iters = nullptr, *ustat = nullptr, *pstat = nullptr, *dropped = nullptr;
+  double *ratio = nullptr;
+  int *iters = nullptr, *sweeps = nullptr, *ustat = nullptr, *pstat = nullptr, *dropped = nullptr;
   double *E = nullptr, *phi = nullptr;
   const double **par_ptr = nullptr;
   double *par_w = nullptr;
@@ -51,9 +51,7 @@ struct mch_handle {
   int R = 0, nc = 0, nq = 0, slots = 0;
   std::vector<Level> lv;
   // scratch shared by the levels (solved one after another)
-  double *r64 = nullptr, *yfine = nullptr, *yc = nullptr;
-  void *vec = nullptr;
-  size_t vec_bytes = 0;
+  double *yfine = nullptr, *yc = nullptr;
   std::vector<void *> allocs;
   std::string err;
   long long h2d = 0, d2h = 0;
@@ -195,7 +193,7 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
   for (int l = 0; l < d.n_levels; ++l) {
     if (d.n_fine % scale) { delete h; return MCH_ERR_ARG; }
     const int n = d.n_fine / scale;
-    if (!pcg2d_supported(n, d.periods, d.precision == MCH_FP64)) {
+    if (!level2d_supported(n, d.periods, d.precision == MCH_FP64)) {
       delete h;
       return MCH_ERR_UNSUPPORTED;
     }
@@ -237,9 +235,8 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
     ALLOC(L.x, np * R * L.nv);
     ALLOC(L.minv, np * L.nv);
     if (l > 0) ALLOC(L.b, np * R * L.nv);
-    ALLOC(L.rho0, np * R);
     ALLOC(L.ratio, np * R);
-    ALLOC(L.done, np * R);
+    ALLOC(L.sweeps, np * R);
     ALLOC(L.iters, np * R);
     ALLOC(L.ustat, np * R);
     ALLOC(L.pstat, np);
@@ -264,16 +261,8 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
       if (e != cudaSuccess) { mch_destroy(h); return MCH_ERR_CUDA; }
     }
   }
-  ALLOC(h->r64, max_unit_nv);
   ALLOC(h->yc, max_unit_nvc);
   if (max_fine) ALLOC(h->yfine, max_fine);
-  {
-    const size_t esz = d.precision == MCH_FP64 ? sizeof(double) : sizeof(float);
-    h->vec_bytes = max_unit_nv * esz;
-    char *v = nullptr;
-    ALLOC(v, h->vec_bytes);
-    h->vec = v;
-  }
 #undef ALLOC
   cudaError_t e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) { mch_destroy(h); return MCH_ERR_CUDA; }
@@ -349,7 +338,7 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
 
   // phase marks for optional event timing: tag 0 setup, 1 interp, 2 pcg, 3 prep, 4 final
   std::vector<int> tags;
-  const bool timing = h->timing && 3 + 2 * d.max_refine + 2 <= 32;
+  const bool timing = h->timing;
   auto mark = [&](int tag) -> cudaError_t {
     if (!timing) return cudaSuccess;
     tags.push_back(tag);
@@ -387,38 +376,21 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
     CK(mark(1), "event");
   }
 
-  // ---- constrained solves: FP64 refinement around PCG sweeps
-  CK(cudaMemsetAsync(L.x, 0, np * R * L.nv * sizeof(double), st), "zero x");
-  CK(cudaMemsetAsync(h->r64, 0, np * R * L.nv * sizeof(double), st), "zero r");
-  CK(cudaMemsetAsync(h->vec, 0, h->vec_bytes, st), "zero vec");
-  CK(cudaMemsetAsync(L.done, 0, np * R * sizeof(int), st), "zero done");
-  CK(cudaMemsetAsync(L.iters, 0, np * R * sizeof(int), st), "zero iters");
-  CK(cudaMemsetAsync(L.ustat, 0, np * R * sizeof(int), st), "zero status");
-  PrepArgs pa{(int)np, R, L.n, P, N, nc, L.nv, L.kappa, L.Sinv64, L.minv, L.labels, g, bvec, L.x,
-              h->r64, h->vec, fp64 ? 1 : 0, 0, ilog2(L.n / P), ilog2(P), L.rho0, L.ratio,
-              L.done, d.rtol};
-  CK(launch_prep2d(pa, st), "prep");
-  ++h->launches;
-  CK(mark(3), "event");
+  // ---- constrained solves: one persistent launch (FP64 refinement around inner sweeps)
   const int max_iter = d.max_iter > 0 ? d.max_iter : 4 * L.n + 50;
-  for (int sweep = 0; sweep < d.max_refine; ++sweep) {
-    if (fp64) {
-      PcgArgs<double> ga{(int)np, R, L.n, P, N, nc, L.nv, L.kappa, L.labels, L.Sinv64,
-                         reinterpret_cast<double *>(h->vec), L.done, L.iters, L.ustat,
-                         (float)d.inner_tol, max_iter, ilog2(L.n / P), ilog2(P)};
-      CK(launch_pcg2d<double>(ga, st, &h->launches), "pcg fp64");
-    } else {
-      PcgArgs<float> ga{(int)np, R, L.n, P, N, nc, L.nv, L.kappa, L.labels, L.Sinv32,
-                        reinterpret_cast<float *>(h->vec), L.done, L.iters, L.ustat,
-                        (float)d.inner_tol, max_iter, ilog2(L.n / P), ilog2(P)};
-      CK(launch_pcg2d<float>(ga, st, &h->launches), "pcg fp32");
-    }
-    CK(mark(2), "event");
-    pa.have_delta = 1;
-    CK(launch_prep2d(pa, st), "prep");
-    ++h->launches;
-    CK(mark(3), "event");
+  if (fp64) {
+    LevelArgs<double> la{(int)np, R, L.n, P, N, nc, L.nv, ilog2(L.n / P), ilog2(P), L.kappa,
+                         L.labels, L.Sinv64, L.Sinv64, L.minv, g, bvec, L.x, L.iters, L.sweeps,
+                         L.ratio, L.ustat, (float)d.inner_tol, max_iter, d.rtol, d.max_refine};
+    CK(launch_level2d<double>(la, st), "level fp64");
+  } else {
+    LevelArgs<float> la{(int)np, R, L.n, P, N, nc, L.nv, ilog2(L.n / P), ilog2(P), L.kappa,
+                        L.labels, L.Sinv32, L.Sinv64, L.minv, g, bvec, L.x, L.iters, L.sweeps,
+                        L.ratio, L.ustat, (float)d.inner_tol, max_iter, d.rtol, d.max_refine};
+    CK(launch_level2d<float>(la, st), "level fp32");
   }
+  ++h->launches;
+  CK(mark(2), "event");
 
   // ---- effective coefficients and the cell functions on the level-1 grid
   ApplyArgs ac{(int)np, R, L.n, 1, L.nv, L.kappa, L.x, bvec, -2.0, h->yc};
@@ -435,12 +407,15 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
   CK(mark(4), "event");
 
   // ---- convergence record
-  std::vector<int> iters(np * R), ustat(np * R), pstat(np), dropped(np);
+  std::vector<int> iters(np * R), sweeps(np * R), ustat(np * R), pstat(np), dropped(np);
   std::vector<double> ratio(np * R);
   CK(cudaMemcpyAsync(iters.data(), L.iters, iters.size() * sizeof(int), cudaMemcpyDeviceToHost, st),
      "read iters");
   CK(cudaMemcpyAsync(ustat.data(), L.ustat, ustat.size() * sizeof(int), cudaMemcpyDeviceToHost, st),
      "read status");
+  CK(cudaMemcpyAsync(sweeps.data(), L.sweeps, sweeps.size() * sizeof(int), cudaMemcpyDeviceToHost,
+                     st),
+     "read sweeps");
   CK(cudaMemcpyAsync(pstat.data(), L.pstat, pstat.size() * sizeof(int), cudaMemcpyDeviceToHost, st),
      "read pstat");
   CK(cudaMemcpyAsync(dropped.data(), L.dropped, dropped.size() * sizeof(int),
@@ -476,8 +451,8 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
     }
     if (!(rr < d.rtol)) notconv = true;
   }
-  S.sweeps = d.max_refine;
-  S.pcg_launches = d.max_refine;
+  for (size_t u = 0; u < np * R; ++u) S.sweeps = std::max(S.sweeps, sweeps[u]);
+  S.pcg_launches = 1;
   for (size_t u = 0; u < np * R; ++u)
     S.pcg_node_iters += (long long)iters[u] * (long long)(L.n - 1) * (L.n - 1);
   for (size_t k = 1; k < tags.size(); ++k) {

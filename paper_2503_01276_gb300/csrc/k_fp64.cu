@@ -1,8 +1,8 @@
-// FP64 kernels of the level solve: the refinement step around the PCG sweeps, the Q1
-// stencil apply on batches of vectors, the nested prolongation/restriction, the
-// interpolation of parent cell functions, the fine-grid constraint functional and the
-// Gram reduction of the effective coefficients. These run in FP64 because they either set
-// the accuracy of the final answer (residuals, constraints, Gram sums) or feed it directly.
+// FP64 kernels of the level solve: the Q1 stencil apply on batches of vectors, the nested
+// prolongation/restriction, the interpolation of parent cell functions, the fine-grid
+// constraint functional and the Gram reduction of the effective coefficients. They run in
+// FP64 because they either set the accuracy of the final answer (constraints, Gram sums)
+// or feed it directly.
 #include "common.cuh"
 #include "kernels.h"
 
@@ -11,160 +11,6 @@ namespace mch {
 namespace {
 
 constexpr int PREP_THREADS = 512;
-
-// Accumulates Ct v over the CTA's node rows into bins (shared), one row at a time with a
-// flush whenever the next row leaves the current sub-block row. `val(kx, ky)` returns the
-// node value (called only for interior nodes of active lanes). Every thread of the CTA must
-// call it. n >= 16 lanes per row; rows are split into contiguous strips per row group.
-template <typename F>
-__device__ void ct_accumulate(int n, int lgm, int lgP, int N, const uint8_t *lab, double *bins,
-                              F val) {
-  const int tid = threadIdx.x;
-  const int c = tid % n, g = tid / n;
-  const int RG = PREP_THREADS / n;
-  const int rpt = (n - 1 + RG - 1) / RG;
-  const bool col_active = c < n - 1;
-  const int kx = c + 1;
-  const int cE = c + 1 <= n - 1 ? c + 1 : n - 1;
-  double acc[MCH_MAX_CONT] = {0, 0, 0, 0};
-  Strip s;
-  s.init(n, lgm, lgP, c, g * rpt, 1);
-  for (int i = 0; i < rpt; ++i) {
-    const int ky = 1 + g * rpt + i;
-    const bool act = col_active && ky <= n - 1;
-    if (act) {
-      const double v = val(kx, ky);
-      scatter_node(s, ky, lab[c + n * (ky - 1)], lab[cE + n * (ky - 1)], lab[c + n * ky],
-                   lab[cE + n * ky], v, acc, bins);
-    }
-    const int kyn = ky + 1;
-    const bool last = (i == rpt - 1);
-    if (last || ((kyn - 1) >> lgm) != ((ky - 1) >> lgm)) {
-      flush_acc(s, acc, N, bins, true);
-#pragma unroll
-      for (int j = 0; j < MCH_MAX_CONT; ++j) acc[j] = 0.0;
-      s.init(n, lgm, lgP, c, kyn - 1, 1);
-    }
-  }
-}
-
-template <typename F>
-__device__ void for_own_nodes(int n, F f) {
-  const int tid = threadIdx.x;
-  const int c = tid % n, g = tid / n;
-  const int RG = PREP_THREADS / n;
-  const int rpt = (n - 1 + RG - 1) / RG;
-  if (c >= n - 1) return;
-  for (int i = 0; i < rpt; ++i) {
-    const int ky = 1 + g * rpt + i;
-    if (ky <= n - 1) f(c + 1, ky);
-  }
-}
-
-__device__ __forceinline__ double node_ct(const uint8_t *lab, int n, int lgm, int lgP, int kx,
-                                          int ky, const double *lam) {
-  auto bin = [&](int ex, int ey) {
-    return (lab[ex + n * ey] << (2 * lgP)) + ((ey >> lgm) << lgP) + (ex >> lgm);
-  };
-  return lam[bin(kx - 1, ky - 1)] + lam[bin(kx, ky - 1)] + lam[bin(kx - 1, ky)] + lam[bin(kx, ky)];
-}
-
-__device__ __forceinline__ double node_apply(const double *kap, int n, const double *x, int kx,
-                                             int ky) {
-  const int W = n + 1;
-  const double *xr = x + kx + W * ky;
-  return q1_apply(kap[(kx - 1) + n * (ky - 1)], kap[kx + n * (ky - 1)], kap[(kx - 1) + n * ky],
-                  kap[kx + n * ky], xr[-W - 1], xr[-W], xr[-W + 1], xr[-1], xr[0], xr[1],
-                  xr[W - 1], xr[W], xr[W + 1]);
-}
-
-// Small dense product out[i] = sum_j Sinv[i][j] v[j] by the first nc threads.
-__device__ __forceinline__ void small_matvec(const double *Si, const double *v, double *out,
-                                             int nc) {
-  const int t = threadIdx.x;
-  if (t < nc) {
-    double s = 0.0;
-    for (int j = 0; j < nc; ++j) s += Si[t * nc + j] * v[j];
-    out[t] = s;
-  }
-}
-
-template <typename TI>
-__global__ void __launch_bounds__(PREP_THREADS) k_prep2d(PrepArgs a) {
-  const int unit = blockIdx.x;
-  if (a.done[unit]) return;
-  const int pt = unit / a.R, r = unit % a.R;
-  const int n = a.n, nc = a.nc, P = a.P, N = a.N, R = a.R;
-  const double *kap = a.kappa + (size_t)pt * n * n;
-  const uint8_t *lab = a.labels + (size_t)pt * n * n;
-  const double *Si = a.Sinv64 + (size_t)pt * nc * nc;
-  double *x = a.x + (size_t)unit * a.nv;
-  double *r64 = a.r64 + (size_t)unit * a.nv;
-  TI *vec = reinterpret_cast<TI *>(a.vec) + (size_t)unit * a.nv;
-  const double *b = a.b ? a.b + (size_t)unit * a.nv : nullptr;
-  const double *mv = a.minv + (size_t)pt * a.nv;
-  const int W = n + 1;
-
-  __shared__ double bins[MCH_MAX_NC], gres[MCH_MAX_NC], mu[MCH_MAX_NC], red[PREP_THREADS / 32];
-  const int tid = threadIdx.x;
-  for (int t = tid; t < nc; t += PREP_THREADS) bins[t] = 0.0;
-  __syncthreads();
-
-  // A. fold in the last correction, accumulate Ct x
-  const bool hd = a.have_delta != 0;
-  ct_accumulate(n, a.lgm, a.lgP, N, lab, bins, [&](int kx, int ky) {
-    const int k = kx + W * ky;
-    double v = x[k];
-    if (hd) {
-      v += (double)vec[k];
-      x[k] = v;
-    }
-    return v;
-  });
-  __syncthreads();
-  // B. mu = S^-1 (g - Ct x)
-  if (tid < nc) gres[tid] = a.g[((size_t)pt * nc + tid) * R + r] - bins[tid];
-  __syncthreads();
-  small_matvec(Si, gres, mu, nc);
-  __syncthreads();
-  if (tid < nc) bins[tid] = 0.0;
-  // C. x += M^-1 Ct^T mu (restores Ct x = g)
-  for_own_nodes(n, [&](int kx, int ky) {
-    const int k = kx + W * ky;
-    x[k] += mv[k] * node_ct(lab, n, a.lgm, a.lgP, kx, ky, mu);
-  });
-  __syncthreads();
-  // D. r = b - A x, accumulate Ct M^-1 r
-  ct_accumulate(n, a.lgm, a.lgP, N, lab, bins, [&](int kx, int ky) {
-    const int k = kx + W * ky;
-    const double rr = (b ? b[k] : 0.0) - node_apply(kap, n, x, kx, ky);
-    r64[k] = rr;
-    return mv[k] * rr;
-  });
-  __syncthreads();
-  small_matvec(Si, bins, mu, nc);
-  __syncthreads();
-  // E. projected residual r - Ct^T lambda, its M^-1 norm, output for the next sweep
-  double rho = 0.0;
-  for_own_nodes(n, [&](int kx, int ky) {
-    const int k = kx + W * ky;
-    const double rt = r64[k] - node_ct(lab, n, a.lgm, a.lgP, kx, ky, mu);
-    rho += rt * rt * mv[k];
-    vec[k] = (TI)rt;
-  });
-  rho = warp_sum(rho);
-  if ((tid & 31) == 0) red[tid >> 5] = rho;
-  __syncthreads();
-  if (tid == 0) {
-    double s = 0.0;
-    for (int w = 0; w < PREP_THREADS / 32; ++w) s += red[w];
-    if (!hd) a.rho0[unit] = s;
-    const double r0 = hd ? a.rho0[unit] : s;
-    const double ratio = r0 > 0.0 ? sqrt(s / r0) : 0.0;
-    a.ratio[unit] = ratio;
-    if (!(ratio >= a.rtol)) a.done[unit] = 1;
-  }
-}
 
 __global__ void k_apply2d(ApplyArgs a) {
   const int unit = blockIdx.y;
@@ -353,12 +199,6 @@ __global__ void __launch_bounds__(GRAM_THREADS)
 }
 
 }  // namespace
-
-cudaError_t launch_prep2d(const PrepArgs &a, cudaStream_t st) {
-  if (a.inner_fp64) k_prep2d<double><<<a.npts * a.R, PREP_THREADS, 0, st>>>(a);
-  else k_prep2d<float><<<a.npts * a.R, PREP_THREADS, 0, st>>>(a);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_apply2d(const ApplyArgs &a, cudaStream_t st) {
   const int W = a.n + 1;

@@ -21,50 +21,30 @@ struct SetupArgs {
 };
 cudaError_t launch_setup2d(const SetupArgs &a, cudaStream_t st);
 
-// Projected PCG sweep on the level grid: solves min 1/2 d'A d - r'd subject to Ct d = 0 for
-// every (point, function) unit whose flag is 0, starting from d = 0 with the projected
-// residual r stored in `vec`, and overwrites `vec` with d. T = float (mixed) or double.
+// Persistent level solve (k_level.cuh): for every (point, function) unit, FP64 refinement
+// steps around inner projected-PCG sweeps, all on chip; writes the FP64 solution x.
 template <typename T>
-struct PcgArgs {
-  int npts, R, n, P, N, nc, nv;
+struct LevelArgs {
+  int npts, R, n, P, N, nc, nv, lgm, lgP;
   const double *kappa;    // [pt][n*n]
   const uint8_t *labels;  // [pt][n*n]
-  const T *Sinv;          // [pt][nc][nc]
-  T *vec;                 // [pt][R][nv]
-  const int *done;        // [pt*R] unit already converged (skip)
-  int *iters;             // [pt*R] accumulated iterations
-  int *status;            // [pt*R] |= 1 on breakdown
-  float tol;              // stop when sqrt(rho / rho0) < tol
-  int max_iter;
-  int lgm, lgP;           // log2(n / P), log2(P)
-};
-template <typename T>
-cudaError_t launch_pcg2d(const PcgArgs<T> &a, cudaStream_t st, int *launches);
-bool pcg2d_supported(int n, int P, bool fp64);
-
-// FP64 refinement step for every (point, function) unit not yet converged: folds the last
-// PCG correction into x, restores the constraints exactly (x += M^-1 Ct^T S^-1 (g - Ct x)),
-// forms the residual b - A x, projects it (r - Ct^T S^-1 Ct M^-1 r), measures
-// rho = r'M^-1 r against the unit's first value and writes the projected residual for the
-// next PCG sweep (as T_inner) unless converged.
-struct PrepArgs {
-  int npts, R, n, P, N, nc, nv;
-  const double *kappa, *Sinv64, *minv;
-  const uint8_t *labels;
+  const T *Sinv;          // [pt][nc][nc] inner precision
+  const double *Sinv64;   // [pt][nc][nc]
+  const double *minv64;   // [pt][nv]
   const double *g;        // [pt][nc][R] scaled targets of this level's problem
   const double *b;        // [pt][R][nv] right-hand side (null = 0)
-  double *x;              // [pt][R][nv]
-  double *r64;            // [pt][R][nv] scratch
-  void *vec;              // [pt][R][nv] inner vector (float or double): in delta, out residual
-  int inner_fp64;
-  int have_delta;
-  int lgm, lgP;           // log2(n / P), log2(P)
-  double *rho0;           // [pt*R]
-  double *ratio;          // [pt*R]
-  int *done;              // [pt*R]
-  double rtol;
+  double *x;              // [pt][R][nv] solution
+  int *iters, *sweeps;    // [pt*R]
+  double *ratio;          // [pt*R] final sqrt(rho / rho_first) of the FP64 projected residual
+  int *status;            // [pt*R] 1 = breakdown
+  float tol;              // inner sweep tolerance
+  int max_iter;           // inner iterations per sweep
+  double rtol;            // refinement tolerance
+  int max_refine;         // inner sweeps
 };
-cudaError_t launch_prep2d(const PrepArgs &a, cudaStream_t st);
+template <typename T>
+cudaError_t launch_level2d(const LevelArgs<T> &a, cudaStream_t st);
+bool level2d_supported(int n, int P, bool fp64);
 
 // y = A(kappa) x + cb * b on an n-grid whose kappa lives on the (n/rho)-grid (piecewise
 // constant), for a batch of vectors; FP64.
