@@ -30,7 +30,7 @@ struct Level {
   int n = 0, rho = 1, npts = 0, nv = 0, nvf = 0;
   double *kappa = nullptr;
   uint8_t *labels = nullptr;
-  double *G = nullptr, *gI = nullptr, *Sinv64 = nullptr;
+  double *G = nullptr, *gI = nullptr, *Sinv64 = nullptr, *Sacc = nullptr, *bacc = nullptr;
   float *Sinv32 = nullptr;
   double *x = nullptr, *b = nullptr, *minv = nullptr;
   double *ratio = nullptr;
@@ -231,6 +231,8 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
     ALLOC(L.G, np * nc * R);
     ALLOC(L.gI, np * nc * R);
     ALLOC(L.Sinv64, np * nc * nc);
+    ALLOC(L.Sacc, np * nc * nc);
+    ALLOC(L.bacc, np * nc * 3);
     if (d.precision == MCH_MIXED) ALLOC(L.Sinv32, np * nc * nc);
     ALLOC(L.x, np * R * L.nv);
     ALLOC(L.minv, np * L.nv);
@@ -349,10 +351,10 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
 
   // ---- constraint data
   SetupArgs sa{(int)np, L.n, P, N, R, nc, d.rve_len / L.n, d.rve_len, L.kappa, L.labels,
-               L.G, L.Sinv64, L.Sinv32, L.pstat, L.dropped, L.minv, L.nv};
+               L.G, L.Sinv64, L.Sinv32, L.pstat, L.dropped, L.minv, L.nv, L.Sacc, L.bacc};
   CK(mark(-1), "event");
   CK(launch_setup2d(sa, st), "setup");
-  ++h->launches;
+  h->launches += 2;
   CK(mark(0), "event");
 
   const double inv_vol = 1.0 / (d.rve_len * d.rve_len);
@@ -360,17 +362,17 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
   const double *bvec = nullptr;
   if (li > 0) {
     // ---- interpolation and correction right-hand sides (level-1 grid, FP64)
-    CK(launch_interp((int)np, R, L.nvf, h->slots, L.par_ptr, L.par_w, L.phi, st), "interp");
-    ApplyArgs aa{(int)np, R, d.n_fine, L.rho, L.nvf, L.kappa, L.phi, nullptr, 0.0, h->yfine};
-    CK(launch_apply2d(aa, st), "apply fine");
-    CK(launch_gram((int)np, R, L.nvf, L.phi, h->yfine, inv_vol, 0.0, L.E, st), "gram I");
+    CK(cudaMemcpyAsync(L.gI, L.G, np * nc * R * sizeof(double), cudaMemcpyDeviceToDevice, st),
+       "targets copy");
+    CK(cudaMemsetAsync(L.E, 0, np * R * R * sizeof(double), st), "zero E");
+    ChildArgs ca{(int)np, R, d.n_fine, ilog2(L.rho), L.nvf, h->slots, ilog2(d.n_fine / P),
+                 ilog2(P), N, nc, L.par_ptr, L.par_w, L.kappa, L.labels, L.phi, h->yfine,
+                 L.gI, 1.0 / ((double)L.rho * L.rho)};
+    CK(launch_child_fine2d(ca, st), "child fine");
+    CK(launch_gram((int)np, R, L.nvf, L.phi, h->yfine, inv_vol, L.E, st), "gram I");
     CK(launch_restrict2d((int)np, R, d.n_fine, L.rho, h->yfine, L.nvf, -1.0, L.b, L.nv, st),
        "restrict");
-    const double s = 1.0 / ((double)L.rho * L.rho);
-    CK(launch_ctapply2d((int)np, R, d.n_fine, L.rho, P, N, nc, L.labels, L.phi, L.nvf, L.G, s,
-                        L.gI, st),
-       "ct fine");
-    h->launches += 5;
+    h->launches += 3;
     g = L.gI;
     bvec = L.b;
     CK(mark(1), "event");
@@ -395,7 +397,8 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
   // ---- effective coefficients and the cell functions on the level-1 grid
   ApplyArgs ac{(int)np, R, L.n, 1, L.nv, L.kappa, L.x, bvec, -2.0, h->yc};
   CK(launch_apply2d(ac, st), "apply coarse");
-  CK(launch_gram((int)np, R, L.nv, L.x, h->yc, inv_vol, li > 0 ? 1.0 : 0.0, L.E, st), "gram");
+  if (li == 0) CK(cudaMemsetAsync(L.E, 0, np * R * R * sizeof(double), st), "zero E");
+  CK(launch_gram((int)np, R, L.nv, L.x, h->yc, inv_vol, L.E, st), "gram");
   h->launches += 2;
   if (li == 0) {
     CK(cudaMemcpyAsync(L.phi, L.x, np * R * L.nv * sizeof(double), cudaMemcpyDeviceToDevice, st),

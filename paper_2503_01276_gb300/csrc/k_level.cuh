@@ -100,7 +100,7 @@ __device__ __forceinline__ void flush_bins(V (&aW)[NC], V (&aE)[NC], V *bins, in
   }
 }
 
-template <typename T, int NEL, int RG, int RPT, int CL, int NC, int MINB>
+template <typename T, int NEL, int RG, int RPT, int CL, int NC, int MINB, bool SR>
 __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
   using C = ClusterOps<CL>;
   constexpr int THREADS = NEL * RG;
@@ -131,6 +131,9 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
   T *lamw = twarp + NWARPS * NRED;                    // [NWARPS][nc]
   T *mis = lamw + NWARPS * nc;                        // [ROWS][W] M^-1 of own rows
   uint8_t *ls = reinterpret_cast<uint8_t *>(mis + ROWS * W);  // [(ROWS+1)][NEL]
+  // FP64 residual of the own rows between steps (d) and (e) when SR (8-byte aligned)
+  double *rs = reinterpret_cast<double *>(
+      (reinterpret_cast<uintptr_t>(ls + (ROWS + 1) * NEL) + 15) & ~uintptr_t(15));
 
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -242,26 +245,35 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
 
   for (int step = 0;; ++step) {
     // ================= FP64 refinement step =================
-    // (a) fold the correction; (b) Ct x
+    // (a) fold the correction; (b) Ct x by element rows (column sums of node pairs)
     {
       double aW[NC], aE[NC];
 #pragma unroll
       for (int j = 0; j < NC; ++j) aW[j] = aE[j] = 0.0;
       int lS0 = lb[0], lS1 = lb[dEc];
+      double vprev = 0.0;
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
         const int lN0 = lb[(i + 1) * NEL], lN1 = lb[(i + 1) * NEL + dEc];
-        const bool act = i < nact;
         double v = 0.0;
-        if (act) {
+        if (i < nact) {
           v = xb[i * W] + (double)x[i];
           xb[i * W] = v;
         }
         x[i] = T(0);
-        acc_node<NC>(aW, aE, lS0, lS1, lN0, lN1, v, (i == RPT - 1) && next_row && act, red64, lgnq,
-                     baseWn, baseEn);
+        const double u = v + vprev;
+        add_lab<NC>(aW, lS0, u);
+        add_lab<NC>(aE, lS1, u);
+        vprev = v;
         lS0 = lN0;
         lS1 = lN1;
+      }
+      if (!next_row) {
+        add_lab<NC>(aW, lS0, vprev);
+        add_lab<NC>(aE, lS1, vprev);
+      } else if (nact == RPT) {
+        atomicAdd(&red64[(lS0 << lgnq) + baseWn], vprev);
+        atomicAdd(&red64[(lS1 << lgnq) + baseEn], vprev);
       }
       flush_bins<NC>(aW, aE, red64, lane, seg, lgnq, baseW, baseE);
     }
@@ -279,20 +291,22 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
     __syncthreads();
     // (c) x += M^-1 Ct^T mu
     {
-      int lS0 = lb[0], lS1 = lb[dEc];
+      double wprev = v64[(lb[0] << lgnq) + baseW] + v64[(lb[dEc] << lgnq) + baseE];
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
         const int lN0 = lb[(i + 1) * NEL], lN1 = lb[(i + 1) * NEL + dEc];
         const bool act = i < nact;
         const bool nr = (i == RPT - 1) && next_row && act;
-        if (act) xb[i * W] += mg[i * (n + 1)] * ctv(v64, lS0, lS1, lN0, lN1, nr);
-        lS0 = lN0;
-        lS1 = lN1;
+        const double wcur = v64[(lN0 << lgnq) + (nr ? baseWn : baseW)] +
+                            v64[(lN1 << lgnq) + (nr ? baseEn : baseE)];
+        if (act) xb[i * W] += mg[i * (n + 1)] * (wprev + wcur);
+        wprev = wcur;
       }
     }
     push_halo_x();
     C::sync();  // x and its halo final for this step; every rank has read red64[0..nc)
-    // (d) Ct M^-1 r with r = b - A x (FP64); r is formed again in (e) instead of being kept
+    // (d) Ct M^-1 r with r = b - A x (FP64); r kept in shared memory when SR, else formed
+    // again in (e)
     {
       double aW[NC], aE[NC];
 #pragma unroll
@@ -301,6 +315,7 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
       double xW1 = xb[-1], xC1 = xb[0], xE1 = xb[dEx];
       double kS0 = kg[0], kS1 = kg[dEc];
       int lS0 = lb[0], lS1 = lb[dEc];
+      double zprev = 0.0;
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
         const bool act = i < nact;
@@ -310,13 +325,24 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
         double zm = 0.0;
         if (act) {
           const double ax = q1_apply(kS0, kS1, kN0, kN1, xW0, xC0, xE0, xW1, xC1, xE1, xW2, xC2, xE2);
-          zm = mg[i * (n + 1)] * ((bg ? bg[i * (n + 1)] : 0.0) - ax);
+          const double rv = (bg ? bg[i * (n + 1)] : 0.0) - ax;
+          if constexpr (SR) rs[(g * RPT + i) * W + kx] = rv;
+          zm = mg[i * (n + 1)] * rv;
         }
-        acc_node<NC>(aW, aE, lS0, lS1, lN0, lN1, zm, (i == RPT - 1) && next_row && act,
-                     red64 + nc, lgnq, baseWn, baseEn);
+        const double u = zm + zprev;
+        add_lab<NC>(aW, lS0, u);
+        add_lab<NC>(aE, lS1, u);
+        zprev = zm;
         xW0 = xW1; xC0 = xC1; xE0 = xE1;
         xW1 = xW2; xC1 = xC2; xE1 = xE2;
         kS0 = kN0; kS1 = kN1; lS0 = lN0; lS1 = lN1;
+      }
+      if (!next_row) {
+        add_lab<NC>(aW, lS0, zprev);
+        add_lab<NC>(aE, lS1, zprev);
+      } else if (nact == RPT) {
+        atomicAdd(&red64[nc + (lS0 << lgnq) + baseWn], zprev);
+        atomicAdd(&red64[nc + (lS1 << lgnq) + baseEn], zprev);
       }
       flush_bins<NC>(aW, aE, red64 + nc, lane, seg, lgnq, baseW, baseE);
     }
@@ -334,27 +360,40 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
     // (e) projected residual, its M^-1 norm; the next sweep's residual
     {
       double rho_p = 0.0;
-      double xW0 = xb[-W - 1], xC0 = xb[-W], xE0 = xb[-W + dEx];
-      double xW1 = xb[-1], xC1 = xb[0], xE1 = xb[dEx];
-      double kS0 = kg[0], kS1 = kg[dEc];
-      int lS0 = lb[0], lS1 = lb[dEc];
+      double xW0 = 0, xC0 = 0, xE0 = 0, xW1 = 0, xC1 = 0, xE1 = 0, kS0 = 0, kS1 = 0;
+      if constexpr (!SR) {
+        xW0 = xb[-W - 1]; xC0 = xb[-W]; xE0 = xb[-W + dEx];
+        xW1 = xb[-1]; xC1 = xb[0]; xE1 = xb[dEx];
+        kS0 = kg[0]; kS1 = kg[dEc];
+      }
+      double wprev = v64[(lb[0] << lgnq) + baseW] + v64[(lb[dEc] << lgnq) + baseE];
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
         const bool act = i < nact;
-        const double xW2 = xb[(i + 1) * W - 1], xC2 = xb[(i + 1) * W], xE2 = xb[(i + 1) * W + dEx];
-        const double kN0 = act ? kg[(i + 1) * n] : 0.0, kN1 = act ? kg[(i + 1) * n + dEc] : 0.0;
         const int lN0 = lb[(i + 1) * NEL], lN1 = lb[(i + 1) * NEL + dEc];
         const bool nr = (i == RPT - 1) && next_row && act;
+        const double wcur = v64[(lN0 << lgnq) + (nr ? baseWn : baseW)] +
+                            v64[(lN1 << lgnq) + (nr ? baseEn : baseE)];
+        double rv = 0.0;
+        if constexpr (SR) {
+          if (act) rv = rs[(g * RPT + i) * W + kx];
+        } else {
+          const double xW2 = xb[(i + 1) * W - 1], xC2 = xb[(i + 1) * W], xE2 = xb[(i + 1) * W + dEx];
+          const double kN0 = act ? kg[(i + 1) * n] : 0.0, kN1 = act ? kg[(i + 1) * n + dEc] : 0.0;
+          if (act)
+            rv = (bg ? bg[i * (n + 1)] : 0.0) -
+                 q1_apply(kS0, kS1, kN0, kN1, xW0, xC0, xE0, xW1, xC1, xE1, xW2, xC2, xE2);
+          xW0 = xW1; xC0 = xC1; xE0 = xE1;
+          xW1 = xW2; xC1 = xC2; xE1 = xE2;
+          kS0 = kN0; kS1 = kN1;
+        }
         double rt = 0.0;
         if (act) {
-          const double ax = q1_apply(kS0, kS1, kN0, kN1, xW0, xC0, xE0, xW1, xC1, xE1, xW2, xC2, xE2);
-          rt = (bg ? bg[i * (n + 1)] : 0.0) - ax - ctv(v64, lS0, lS1, lN0, lN1, nr);
+          rt = rv - (wprev + wcur);
           rho_p += rt * rt * mg[i * (n + 1)];
         }
         rr[i] = T(rt);
-        xW0 = xW1; xC0 = xC1; xE0 = xE1;
-        xW1 = xW2; xC1 = xC2; xE1 = xE2;
-        kS0 = kN0; kS1 = kN1; lS0 = lN0; lS1 = lN1;
+        wprev = wcur;
       }
       rho_p = warp_sum(rho_p);
       if (lane == 0) atomicAdd(&red64[2 * nc], rho_p);
@@ -406,6 +445,10 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
         T pW1 = pb[-1], pC1 = pb[0], pE1 = pb[dEx];
         T kS0 = kb[0], kS1 = kb[dEc];
         int lS0 = lb[0], lS1 = lb[dEc];
+        T zprev = T(0), mqprev = T(0);
+        // Element row ky-1 (south of row i) gets this thread's column sum of the node pair
+        // (ky-1, ky): only row i's value for i = 0 (the row below belongs to the strip
+        // underneath), both for i > 0. The strip's last element row is added after the loop.
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
           const T pW2 = pb[(i + 1) * W - 1], pC2 = pb[(i + 1) * W], pE2 = pb[(i + 1) * W + dEx];
@@ -422,12 +465,28 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
           zq += z * qv;
           qmq += qv * mq;
           rz += rr[i] * z;
-          const bool tn = (i == RPT - 1) && next_row && act;
-          acc_node<NC>(azW, azE, lS0, lS1, lN0, lN1, z, tn, rb + 4, lgnq, baseWn, baseEn);
-          acc_node<NC>(aqW, aqE, lS0, lS1, lN0, lN1, mq, tn, rb + 4 + nc, lgnq, baseWn, baseEn);
+          const T uz = z + zprev, uq = mq + mqprev;
+          add_lab<NC>(azW, lS0, uz);
+          add_lab<NC>(azE, lS1, uz);
+          add_lab<NC>(aqW, lS0, uq);
+          add_lab<NC>(aqE, lS1, uq);
+          zprev = z;
+          mqprev = mq;
           pW0 = pW1; pC0 = pC1; pE0 = pE1;
           pW1 = pW2; pC1 = pC2; pE1 = pE2;
           kS0 = kN0; kS1 = kN1; lS0 = lN0; lS1 = lN1;
+        }
+        // element row of the strip's top: lS0/lS1 now hold its labels
+        if (!next_row) {
+          add_lab<NC>(azW, lS0, zprev);
+          add_lab<NC>(azE, lS1, zprev);
+          add_lab<NC>(aqW, lS0, mqprev);
+          add_lab<NC>(aqE, lS1, mqprev);
+        } else if (nact == RPT) {
+          atomicAdd(&rb[4 + (lS0 << lgnq) + baseWn], zprev);
+          atomicAdd(&rb[4 + (lS1 << lgnq) + baseEn], zprev);
+          atomicAdd(&rb[4 + nc + (lS0 << lgnq) + baseWn], mqprev);
+          atomicAdd(&rb[4 + nc + (lS1 << lgnq) + baseEn], mqprev);
         }
         flush_bins<NC>(azW, azE, rb + 4, lane, seg, lgnq, baseW, baseE);
         flush_bins<NC>(aqW, aqE, rb + 4 + nc, lane, seg, lgnq, baseW, baseE);
@@ -483,21 +542,22 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
         const T beta = stop ? T(0) : rho_new / rho;
         rho = rho_new;
 
-        lS0 = lb[0];
-        lS1 = lb[dEc];
+        // Ct^T lambda at node (ky) = w(ky-1) + w(ky), w(ey) = lambda of the element row ey's
+        // west and east elements of this column
+        T wprev = lw[(lb[0] << lgnq) + baseW] + lw[(lb[dEc] << lgnq) + baseE];
 #pragma unroll
         for (int i = 0; i < RPT; ++i) {
           const int lN0 = lb[(i + 1) * NEL], lN1 = lb[(i + 1) * NEL + dEc];
           const bool act = i < nact;
           const bool nr = (i == RPT - 1) && next_row && act;
+          const T wcur = lw[(lN0 << lgnq) + (nr ? baseWn : baseW)] +
+                         lw[(lN1 << lgnq) + (nr ? baseEn : baseE)];
           const T p0 = pb[i * W];
           x[i] += alpha * p0;
-          const T cl = ctv(lw, lS0, lS1, lN0, lN1, nr);
-          rr[i] = act ? rr[i] - alpha * q[i] - cl : T(0);
+          rr[i] = act ? rr[i] - alpha * q[i] - (wprev + wcur) : T(0);
           const T pn = mb[i * W] * rr[i] + beta * p0;
           if (act && !stop) pb[i * W] = pn;
-          lS0 = lN0;
-          lS1 = lN1;
+          wprev = wcur;
         }
         if (stop) {
           if (stop == 2) breakdown = true;
@@ -525,7 +585,7 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
   C::sync();  // no CTA leaves while a peer may still read its shared memory
 }
 
-template <typename T, int NEL, int RG, int RPT, int CL>
+template <typename T, int NEL, int RG, int RPT, int CL, bool SR>
 size_t level_smem_bytes(int nc) {
   constexpr int THREADS = NEL * RG;
   constexpr int ROWS = RG * RPT;
@@ -533,14 +593,18 @@ size_t level_smem_bytes(int nc) {
   return sizeof(double) * ((ROWS + 2) * (NEL + 1) + nc * nc + 2 * nc + 1 + 2 * nc + 2) +
          sizeof(T) * ((ROWS + 2) * (NEL + 1) + (ROWS + 1) * NEL + nc * nc + 2 * nred +
                       (THREADS / 32) * (nred + nc) + ROWS * (NEL + 1)) +
-         (ROWS + 1) * NEL + 16;
+         (ROWS + 1) * NEL + 16 + (SR ? sizeof(double) * ROWS * (NEL + 1) : 0);
 }
 
 template <typename T, int NEL, int RG, int RPT, int CL, int NC, int MINB>
 cudaError_t launch_level_cfg(const LevelArgs<T> &a, cudaStream_t st) {
   constexpr int THREADS = NEL * RG;
-  const size_t smem = level_smem_bytes<T, NEL, RG, RPT, CL>(a.nc);
-  auto kern = k_level2d<T, NEL, RG, RPT, CL, NC, MINB>;
+  // keep the FP64 residual on chip when it fits beside everything else
+  constexpr bool SR = (size_t)RG * RPT * (NEL + 1) * 8 + 40 * 1024 +
+                          (size_t)(RG * RPT + 2) * (NEL + 1) * (8 + sizeof(T)) * 2 <=
+                      200 * 1024;
+  const size_t smem = level_smem_bytes<T, NEL, RG, RPT, CL, SR>(a.nc);
+  auto kern = k_level2d<T, NEL, RG, RPT, CL, NC, MINB, SR>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};

@@ -18,6 +18,8 @@ struct SetupArgs {
   int *dropped;           // [pt]
   double *minv;           // [pt][nv] 1 / diag(A) at interior nodes (0 elsewhere)
   int nv;
+  double *Sacc;           // [pt][nc][nc] scratch accumulator of S
+  double *bacc;           // [pt][nc][3] scratch: element count, centroid sums per row
 };
 cudaError_t launch_setup2d(const SetupArgs &a, cudaStream_t st);
 
@@ -59,26 +61,31 @@ struct ApplyArgs {
 cudaError_t launch_apply2d(const ApplyArgs &a, cudaStream_t st);
 
 // out_coarse = scale * P^T y_fine (restriction by the transpose of the nested bilinear
-// prolongation), coarse grid n_c = n_f / rho.
+// prolongation), coarse grid n_c = n_f / rho, rho in {2, 4, 8}.
 cudaError_t launch_restrict2d(int npts, int R, int nf, int rho, const double *yf, int nvf,
                               double scale, double *outc, int nvc, cudaStream_t st);
 
-// phi_fine += P x_coarse.
+// phi_fine += P x_coarse, rho in {2, 4, 8}.
 cudaError_t launch_prolong_add2d(int npts, int R, int nf, int rho, const double *xc, int nvc,
                                  double *phif, int nvf, cudaStream_t st);
 
-// I[pt][r] = sum_t w[pt][t] Phi_{parent t}[r] on the fine lattice.
-cudaError_t launch_interp(int npts, int R, int nvf, int slots, const double *const *par_ptr,
-                          const double *par_w, double *I, cudaStream_t st);
+// Fine-grid work of a child level (k_child.cu): I = sum_t w_t Phi_t into phi, y = A_1 I, and
+// g -= s * C_1 I (g holds the targets on entry).
+struct ChildArgs {
+  int npts, R, nf, lgr, nvf, slots, lgmf, lgP, N, nc;
+  const double *const *par_ptr;   // [pt][slots] parent cell functions (R vectors each)
+  const double *par_w;            // [pt][slots]
+  const double *kappa_c;          // [pt][(nf >> lgr)^2]
+  const uint8_t *labels_c;        // [pt][(nf >> lgr)^2]
+  double *phi;                    // [pt][R][nvf]
+  double *y;                      // [pt][R][nvf]
+  double *g;                      // [pt][nc][R]
+  double s;                       // rho^-2
+};
+cudaError_t launch_child_fine2d(const ChildArgs &a, cudaStream_t st);
 
-// g[pt][b][r] = G[pt][b][r] - s * (Ct_fine v)[b] with the fine-grid constraint rows of the
-// labels prolonged from the coarse grid (n_c = n_f / rho).
-cudaError_t launch_ctapply2d(int npts, int R, int nf, int rho, int P, int N, int nc,
-                             const uint8_t *labels_c, const double *v, int nvf,
-                             const double *G, double s, double *g, cudaStream_t st);
-
-// E[pt][r][s] = beta * E + alpha * 1/2 sum_k (X_r Y_s + Y_r X_s).
+// E[pt][r][s] += alpha * 1/2 sum_k (X_r Y_s + Y_r X_s), R in {3, 6, 9, 12}.
 cudaError_t launch_gram(int npts, int R, int nv, const double *X, const double *Y,
-                        double alpha, double beta, double *E, cudaStream_t st);
+                        double alpha, double *E, cudaStream_t st);
 
 }  // namespace mch
