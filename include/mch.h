@@ -164,6 +164,30 @@ mch_status mch_level_stats_get(const mch_handle *h, int level, mch_level_stats *
  * n = 1..L. Requires every level solved with keep_parents = 1. */
 mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const *dL_dkappa);
 
+/* Size of the fixed device buffer used by mch_direct_noalloc (32 MiB per GPU that loads the
+ * library, held until the process exits). */
+#define MCH_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/* Effective coefficients of one level without a hierarchy (every point solved directly on
+ * its n_elem^2 grid, as at level 1) for n_points macropoints, computed WITHOUT ALLOCATING any
+ * device memory. For callers that cannot allocate when they need the result: device memory
+ * already reserved by another framework's caching allocator, a fixed memory budget fixed at
+ * start-up, or a latency-sensitive path where cudaMalloc/cudaFree would synchronise the
+ * device. All intermediate data lives in one library-owned buffer of
+ * MCH_NOALLOC_SCRATCH_BYTES; a batch that does not fit returns MCH_ERR_OOM (about 140 KB per
+ * point at n_elem = 32 and 470 KB at n_elem = 64 with two continua).
+ *   kappa [n_points][n_elem^2] FP64, labels [n_points][n_elem^2] uint8: device memory.
+ *   E [n_points][R][R] FP64, R = n_cont * 3: device memory, overwritten.
+ *   precision MCH_MIXED or MCH_FP64; rtol as in mch_desc (0 -> 1e-8). 2D only.
+ * Work is enqueued on cuda_stream (a cudaStream_t, NULL = legacy default stream), which is
+ * synchronised once before returning. The first call on a device looks up the buffer's
+ * device address while that device is current, so make it before any stream capture. Calls
+ * share the buffer: calls that overlap on the GPU (other streams, other host threads) race.
+ * The paper has no counterpart to this entry point. */
+mch_status mch_direct_noalloc(int n_cont, int n_elem, int periods, double rve_len, int precision,
+                              double rtol, int n_points, const double *kappa,
+                              const uint8_t *labels, double *E, void *cuda_stream);
+
 /* Releases every library-owned buffer. Safe on NULL. */
 void mch_destroy(mch_handle *h);
 

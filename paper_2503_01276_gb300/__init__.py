@@ -6,7 +6,7 @@ marshals arguments to it. The library is loaded on first use of any name below, 
 raises ImportError if it has not been built (``paper_2503_01276_gb300.build.build()``).
 """
 _EXPORTS = ("MCH_FP64", "MCH_MIXED", "LIB_PATH", "MchDesc", "MchError", "Solver",
-            "desc_from_workload", "load_library", "make_desc", "plan_level")
+            "desc_from_workload", "direct_noalloc", "load_library", "make_desc", "plan_level")
 
 __all__ = list(_EXPORTS)
 

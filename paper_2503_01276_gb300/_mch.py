@@ -63,6 +63,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "mch_level_stats_get": (C.c_int, [P, C.c_int, C.POINTER(MchLevelStats)]),
         "mch_set_timing": (C.c_int, [P, C.c_int]),
         "mch_backward": (C.c_int, [P, P, P]),
+        "mch_direct_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
+                                         C.c_double, C.c_int, P, P, P, P]),
         "mch_destroy": (None, [P]),
         "mch_last_error": (C.c_char_p, [P]),
         "mch_status_name": (C.c_char_p, [C.c_int]),
@@ -111,6 +113,22 @@ def desc_from_workload(wl, **kw) -> MchDesc:
                 precision=wl.precision)
     args.update(kw)
     return make_desc(**args)
+
+
+def direct_noalloc(n_cont, n_elem, periods, rve_len, kappa, labels, E, precision="mixed",
+                   rtol=0.0, stream=None) -> int:
+    """Single-level effective coefficients through mch_direct_noalloc (no device allocation;
+    kappa, labels and E must be device buffers). Returns the status code."""
+    if stream is None:
+        try:
+            import torch
+            stream = torch.cuda.current_stream().cuda_stream
+        except Exception:
+            stream = 0
+    npts = int(kappa.shape[0])
+    return _LIB.mch_direct_noalloc(n_cont, n_elem, periods, rve_len,
+                                   MCH_FP64 if precision == "fp64" else MCH_MIXED, rtol, npts,
+                                   _ptr(kappa), _ptr(labels), _ptr(E), C.c_void_p(stream))
 
 
 def plan_level(desc: MchDesc, level: int):
