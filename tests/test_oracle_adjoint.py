@@ -1,0 +1,62 @@
+"""Pins of the oracle's gradient: central finite differences of the loss on elements of
+every level (the loss is recomputed through the whole hierarchy, so a parent's kappa
+reaches its children's coefficients), and the Euler identity sum kappa dL/dkappa = L, which
+holds because every effective coefficient is 1-homogeneous in kappa jointly over levels
+(scaling all kappa leaves every cell function unchanged, Sec. 3, Eq. phi_abstract)."""
+import numpy as np
+import pytest
+
+import mch_inputs as mi
+from oracle import adjoint, plan
+
+
+def _setup(strides, n_fine, macro, seed=7):
+    wl = mi.small_workload("channel2d_17x17_L3", n_fine=n_fine, macro_n=macro,
+                           strides=strides)
+    pl = plan.level_plan(wl)
+    med = [mi.media(wl, l["points"], wl.n_level(k + 1)) for k, l in enumerate(pl)]
+    rng = np.random.default_rng(seed)
+    W = [rng.standard_normal((len(l["points"]), wl.n_rhs, wl.n_rhs)) for l in pl]
+    return wl, pl, med, W
+
+
+def _loss(wl, pl, med, W):
+    return adjoint.loss(adjoint.forward(wl, pl, med), W)
+
+
+@pytest.mark.parametrize("strides,n_fine,macro", [((1,), 16, 3), ((2, 1), 16, 3),
+                                                  ((4, 2, 1), 32, 5)])
+def test_euler_identity(strides, n_fine, macro):
+    wl, pl, med, W = _setup(strides, n_fine, macro)
+    fwd = adjoint.forward(wl, pl, med)
+    Lv = adjoint.loss(fwd, W)
+    g = adjoint.backward(wl, pl, med, fwd, W)
+    s = sum(float(np.sum(med[n][0] * g[n])) for n in range(len(pl)))
+    assert abs(s - Lv) <= 1e-10 * abs(Lv)
+
+
+@pytest.mark.parametrize("strides,n_fine,macro", [((1,), 16, 3), ((2, 1), 16, 3),
+                                                  ((4, 2, 1), 32, 5)])
+def test_central_differences(strides, n_fine, macro):
+    wl, pl, med, W = _setup(strides, n_fine, macro)
+    fwd = adjoint.forward(wl, pl, med)
+    g = adjoint.backward(wl, pl, med, fwd, W)
+    rng = np.random.default_rng(11)
+    checked = 0
+    for n in range(len(pl)):
+        kap, lab = med[n]
+        npts, ne = kap.shape
+        for _ in range(3):
+            i = int(rng.integers(npts))
+            e = int(rng.integers(ne))
+            h = 1e-6 * kap[i, e]
+            out = []
+            for sgn in (+1, -1):
+                k2 = [m[0].copy() for m in med]
+                k2[n][i, e] += sgn * h
+                out.append(_loss(wl, pl, [(k2[q], med[q][1]) for q in range(len(pl))], W))
+            fd = (out[0] - out[1]) / (2 * h)
+            scale = max(abs(g[n][i, e]), 1e-6 * np.abs(g[n]).max())
+            assert abs(fd - g[n][i, e]) <= 1e-5 * scale + 1e-9 * abs(out[0]) / h, (n, i, e, fd, g[n][i, e])
+            checked += 1
+    assert checked == 3 * len(pl)
