@@ -25,7 +25,7 @@ def _loss(wl, pl, med, W):
 
 
 @pytest.mark.parametrize("strides,n_fine,macro", [((1,), 16, 3), ((2, 1), 16, 3),
-                                                  ((4, 2, 1), 32, 5)])
+                                                  ((4, 2, 1), 64, 5)])
 def test_euler_identity(strides, n_fine, macro):
     wl, pl, med, W = _setup(strides, n_fine, macro)
     fwd = adjoint.forward(wl, pl, med)
@@ -36,7 +36,7 @@ def test_euler_identity(strides, n_fine, macro):
 
 
 @pytest.mark.parametrize("strides,n_fine,macro", [((1,), 16, 3), ((2, 1), 16, 3),
-                                                  ((4, 2, 1), 32, 5)])
+                                                  ((4, 2, 1), 64, 5)])
 def test_central_differences(strides, n_fine, macro):
     wl, pl, med, W = _setup(strides, n_fine, macro)
     fwd = adjoint.forward(wl, pl, med)
