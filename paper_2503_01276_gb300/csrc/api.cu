@@ -38,6 +38,9 @@ struct Level {
   double *E = nullptr, *phi = nullptr;
   const double **par_ptr = nullptr;
   double *par_w = nullptr;
+  double *lam = nullptr;          // [pt][R][nc] final multipliers of the forward solve
+  double *V = nullptr;            // [pt][R][nvf] backward seeds (levels with children)
+  double **par_V = nullptr;       // [pt][slots] parents' seed blocks (levels > 1)
   bool solved = false;
   mch_level_stats stats{};
 };
@@ -52,6 +55,11 @@ struct mch_handle {
   std::vector<Level> lv;
   // scratch shared by the levels (solved one after another)
   double *yfine = nullptr, *yc = nullptr;
+  // backward-pass buffers, allocated on the first mch_backward
+  bool bw_ready = false;
+  double *psi1 = nullptr, *psi2 = nullptr, *lamadj = nullptr, *gzero = nullptr, *Wd = nullptr,
+         *dk = nullptr, *bw_ratio = nullptr;
+  int *bw_iters = nullptr, *bw_sweeps = nullptr, *bw_status = nullptr;
   std::vector<void *> allocs;
   std::string err;
   long long h2d = 0, d2h = 0;
@@ -236,7 +244,8 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
     if (d.precision == MCH_MIXED) ALLOC(L.Sinv32, np * nc * nc);
     ALLOC(L.x, np * R * L.nv);
     ALLOC(L.minv, np * L.nv);
-    if (l > 0) ALLOC(L.b, np * R * L.nv);
+    ALLOC(L.b, np * R * L.nv);
+    ALLOC(L.lam, np * R * nc);
     ALLOC(L.ratio, np * R);
     ALLOC(L.sweeps, np * R);
     ALLOC(L.iters, np * R);
@@ -383,12 +392,14 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
   if (fp64) {
     LevelArgs<double> la{(int)np, R, L.n, P, N, nc, L.nv, ilog2(L.n / P), ilog2(P), L.kappa,
                          L.labels, L.Sinv64, L.Sinv64, L.minv, g, bvec, L.x, L.iters, L.sweeps,
-                         L.ratio, L.ustat, (float)d.inner_tol, max_iter, d.rtol, d.max_refine};
+                         L.ratio, L.ustat, (float)d.inner_tol, max_iter, d.rtol, d.max_refine,
+                         L.lam};
     CK(launch_level2d<double>(la, st), "level fp64");
   } else {
     LevelArgs<float> la{(int)np, R, L.n, P, N, nc, L.nv, ilog2(L.n / P), ilog2(P), L.kappa,
                         L.labels, L.Sinv32, L.Sinv64, L.minv, g, bvec, L.x, L.iters, L.sweeps,
-                        L.ratio, L.ustat, (float)d.inner_tol, max_iter, d.rtol, d.max_refine};
+                        L.ratio, L.ustat, (float)d.inner_tol, max_iter, d.rtol, d.max_refine,
+                        L.lam};
     CK(launch_level2d<float>(la, st), "level fp32");
   }
   ++h->launches;
@@ -541,8 +552,128 @@ mch_status mch_level_stats_get(const mch_handle *h, int level, mch_level_stats *
 }
 
 mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const *dL_dkappa) {
-  if (!h || !dL_dE || !dL_dkappa) return MCH_ERR_ARG;
-  return set_err(h, MCH_ERR_UNSUPPORTED, "backward pass not built yet");
+  if (!h || !dL_dE || !dL_dkappa) return set_err(h, MCH_ERR_ARG, "bad argument");
+  const mch_desc &d = h->d;
+  const int Lv = d.n_levels, R = h->R, nc = h->nc, N = d.n_cont, P = d.periods;
+  for (int l = 0; l < Lv; ++l) {
+    if (!h->lv[l].solved) return set_err(h, MCH_ERR_ORDER, "every level must be solved first");
+    if (!dL_dE[l] || !dL_dkappa[l]) return set_err(h, MCH_ERR_ARG, "null gradient buffer");
+  }
+  cudaStream_t st = h->st;
+  const int nvf = nv_of(d.n_fine);
+  if (!h->bw_ready) {
+    size_t mfine = 0, munit = 0, mnc = 0, mrr = 0, mel = 0;
+    for (int l = 0; l < Lv; ++l) {
+      const Level &L = h->lv[l];
+      mfine = std::max(mfine, (size_t)L.npts * R * nvf);
+      munit = std::max(munit, (size_t)L.npts * R);
+      mnc = std::max(mnc, (size_t)L.npts * R * nc);
+      mrr = std::max(mrr, (size_t)L.npts * R * R);
+      mel = std::max(mel, (size_t)L.npts * L.n * L.n);
+    }
+#define BALLOC(ptr, cnt)                                               \
+  do {                                                                 \
+    cudaError_t e_ = dalloc(h, &(ptr), (size_t)(cnt));                 \
+    if (e_ != cudaSuccess) return cuda_fail(h, e_, "backward buffers"); \
+  } while (0)
+    BALLOC(h->psi1, mfine);
+    BALLOC(h->psi2, mfine);
+    BALLOC(h->lamadj, mnc);
+    BALLOC(h->gzero, mnc);
+    BALLOC(h->Wd, mrr);
+    BALLOC(h->dk, mel);
+    BALLOC(h->bw_ratio, munit);
+    BALLOC(h->bw_iters, munit);
+    BALLOC(h->bw_sweeps, munit);
+    BALLOC(h->bw_status, munit);
+    for (int l = 0; l + 1 < Lv; ++l) BALLOC(h->lv[l].V, (size_t)h->lv[l].npts * R * nvf);
+    for (int l = 1; l < Lv; ++l) {
+      Level &L = h->lv[l];
+      BALLOC(L.par_V, (size_t)L.npts * h->slots);
+      std::vector<double *> hp((size_t)L.npts * h->slots, nullptr);
+      for (size_t i = 0; i < hp.size(); ++i) {
+        const int pl = L.plan.par_level[i];
+        if (pl > 0) hp[i] = h->lv[pl - 1].V + (size_t)L.plan.par_pos[i] * R * nvf;
+      }
+      CK(cudaMemcpyAsync(L.par_V, hp.data(), hp.size() * sizeof(void *), cudaMemcpyHostToDevice,
+                         st),
+         "seed table");
+      CK(cudaStreamSynchronize(st), "seed table");
+    }
+#undef BALLOC
+    h->bw_ready = true;
+  }
+  h->h2d = h->d2h = 0;
+  for (int l = 0; l + 1 < Lv; ++l)
+    CK(cudaMemsetAsync(h->lv[l].V, 0, (size_t)h->lv[l].npts * R * nvf * sizeof(double), st),
+       "zero seeds");
+  const double inv_vol = 1.0 / (d.rve_len * d.rve_len);
+  const bool fp64 = d.precision == MCH_FP64;
+  double worst = 0.0;
+  bool breakdown = false;
+  for (int li = Lv - 1; li >= 0; --li) {
+    Level &L = h->lv[li];
+    const size_t np = L.npts;
+    CK(stage(h, h->Wd, dL_dE[li], np * R * R * sizeof(double), true), "stage dL/dE");
+    const bool seeds = L.V != nullptr;
+    if (seeds) {
+      // adjoint constrained solve with right-hand side P^T V and zero targets
+      if (L.rho > 1) {
+        CK(launch_restrict2d((int)np, R, d.n_fine, L.rho, L.V, nvf, 1.0, L.b, L.nv, st),
+           "restrict seeds");
+      } else {
+        CK(cudaMemcpyAsync(L.b, L.V, np * R * nvf * sizeof(double), cudaMemcpyDeviceToDevice, st),
+           "copy seeds");
+      }
+      CK(cudaMemsetAsync(h->yc, 0, np * R * L.nv * sizeof(double), st), "zero mu");
+      const int max_iter = d.max_iter > 0 ? d.max_iter : 4 * L.n + 50;
+      if (fp64) {
+        LevelArgs<double> la{(int)np, R, L.n, P, N, nc, L.nv, ilog2(L.n / P), ilog2(P), L.kappa,
+                             L.labels, L.Sinv64, L.Sinv64, L.minv, h->gzero, L.b, h->yc,
+                             h->bw_iters, h->bw_sweeps, h->bw_ratio, h->bw_status,
+                             (float)d.inner_tol, max_iter, d.rtol, d.max_refine, h->lamadj};
+        CK(launch_level2d<double>(la, st), "adjoint fp64");
+      } else {
+        LevelArgs<float> la{(int)np, R, L.n, P, N, nc, L.nv, ilog2(L.n / P), ilog2(P), L.kappa,
+                            L.labels, L.Sinv32, L.Sinv64, L.minv, h->gzero, L.b, h->yc,
+                            h->bw_iters, h->bw_sweeps, h->bw_ratio, h->bw_status,
+                            (float)d.inner_tol, max_iter, d.rtol, d.max_refine, h->lamadj};
+        CK(launch_level2d<float>(la, st), "adjoint fp32");
+      }
+    }
+    AdjArgs aa{(int)np, R, d.n_fine, ilog2(L.rho), nvf, L.nv, nc, ilog2(d.n_fine / P), ilog2(P),
+               h->slots, inv_vol, 1.0 / ((double)L.rho * L.rho), h->Wd, L.phi,
+               seeds ? h->yc : nullptr, L.lam, seeds ? h->lamadj : nullptr, L.kappa, L.labels,
+               L.V, h->psi1, h->psi2, h->dk, L.par_V, L.par_w};
+    CK(launch_adj_combine2d(aa, st), "adjoint combine");
+    CK(launch_adj_grad2d(aa, st), "adjoint gradient");
+    if (li > 0) CK(launch_adj_seed2d(aa, st), "adjoint seeds");
+    CK(stage(h, dL_dkappa[li], h->dk, np * L.n * L.n * sizeof(double), false), "copy dL/dkappa");
+    if (seeds) {
+      std::vector<double> ratio(np * R);
+      std::vector<int> stat(np * R);
+      CK(cudaMemcpyAsync(ratio.data(), h->bw_ratio, ratio.size() * sizeof(double),
+                         cudaMemcpyDeviceToHost, st),
+         "read adjoint ratio");
+      CK(cudaMemcpyAsync(stat.data(), h->bw_status, stat.size() * sizeof(int),
+                         cudaMemcpyDeviceToHost, st),
+         "read adjoint status");
+      CK(cudaStreamSynchronize(st), "adjoint sync");
+      for (size_t u = 0; u < np * R; ++u) {
+        worst = std::max(worst, ratio[u] == ratio[u] ? ratio[u] : 1e300);
+        breakdown |= stat[u] != 0;
+      }
+    }
+  }
+  CK(cudaStreamSynchronize(st), "backward sync");
+  if (breakdown) return set_err(h, MCH_ERR_BREAKDOWN, "adjoint PCG breakdown");
+  if (!(worst < d.rtol)) {
+    char buf[128];
+    snprintf(buf, sizeof buf, "adjoint residual ratio %.3e above rtol %.3e", worst, d.rtol);
+    return set_err(h, MCH_ERR_NOT_CONVERGED, buf);
+  }
+  h->err.clear();
+  return MCH_OK;
 }
 
 }  // extern "C"

@@ -576,6 +576,8 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
 #pragma unroll
   for (int i = 0; i < RPT; ++i)
     if (i < nact) xo[i * (n + 1)] = xb[i * W];
+  if (a.lam && rank == 0)
+    for (int i = tid; i < nc; i += THREADS) a.lam[(size_t)unit * nc + i] = v64[i];
   if (rank == 0 && tid == 0) {
     a.iters[unit] = iters;
     a.sweeps[unit] = sweeps;

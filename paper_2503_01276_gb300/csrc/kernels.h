@@ -43,6 +43,7 @@ struct LevelArgs {
   int max_iter;           // inner iterations per sweep
   double rtol;            // refinement tolerance
   int max_refine;         // inner sweeps
+  double *lam;            // [pt*R][nc] final multipliers (b - A x = Ct^T lam), or null
 };
 template <typename T>
 cudaError_t launch_level2d(const LevelArgs<T> &a, cudaStream_t st);
@@ -87,5 +88,26 @@ cudaError_t launch_child_fine2d(const ChildArgs &a, cudaStream_t st);
 // E[pt][r][s] += alpha * 1/2 sum_k (X_r Y_s + Y_r X_s), R in {3, 6, 9, 12}.
 cudaError_t launch_gram(int npts, int R, int nv, const double *X, const double *Y,
                         double alpha, double *E, cudaStream_t st);
+
+// Backward pass kernels (k_adjoint.cu).
+struct AdjArgs {
+  int npts, R, nf, lgr, nvf, nvc, nc, lgmf, lgP, slots;
+  double inv_vol, inv_rho2;
+  const double *W;          // [pt][R][R] dL/dE
+  const double *phi;        // [pt][R][nvf] cell functions (level-1 grid)
+  const double *mu;         // [pt][R][nvc] adjoint solution, or null
+  const double *lam;        // [pt][R][nc] forward multipliers
+  const double *lamadj;     // [pt][R][nc] adjoint multipliers, or null
+  const double *kappa_c;    // [pt][ncg^2]
+  const uint8_t *labels_c;  // [pt][ncg^2]
+  const double *V;          // [pt][R][nvf] seeds of this level, or null
+  double *psi1, *psi2;      // [pt][R][nvf] scratch
+  double *dkappa;           // [pt][ncg^2]
+  double *const *par_V;     // [pt][slots] parents' seed blocks
+  const double *par_w;      // [pt][slots]
+};
+cudaError_t launch_adj_combine2d(const AdjArgs &a, cudaStream_t st);
+cudaError_t launch_adj_grad2d(const AdjArgs &a, cudaStream_t st);
+cudaError_t launch_adj_seed2d(const AdjArgs &a, cudaStream_t st);
 
 }  // namespace mch

@@ -133,13 +133,13 @@ extern "C" mch_status mch_direct_noalloc(int n_cont, int n_elem, int periods, do
   if (fp64) {
     LevelArgs<double> la{n_points, R, n, P, N, nc, nv, ilog2i(n / P), ilog2i(P), kappa, labels,
                          D(o_S64), D(o_S64), D(o_minv), D(o_G), nullptr, D(o_x), I(o_it),
-                         I(o_sw), D(o_ratio), I(o_ustat), 1e-4f, max_iter, tol, 6};
+                         I(o_sw), D(o_ratio), I(o_ustat), 1e-4f, max_iter, tol, 6, nullptr};
     e = launch_level2d<double>(la, st);
   } else {
     LevelArgs<float> la{n_points, R, n, P, N, nc, nv, ilog2i(n / P), ilog2i(P), kappa, labels,
                         reinterpret_cast<float *>(base + o_S32), D(o_S64), D(o_minv), D(o_G),
                         nullptr, D(o_x), I(o_it), I(o_sw), D(o_ratio), I(o_ustat), 1e-4f,
-                        max_iter, tol, 6};
+                        max_iter, tol, 6, nullptr};
     e = launch_level2d<float>(la, st);
   }
   if (e != cudaSuccess) return MCH_ERR_CUDA;

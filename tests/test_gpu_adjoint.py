@@ -1,0 +1,84 @@
+"""GPU backward pass (mch_backward) against the oracle's gradient and the Euler identity.
+
+Loss L = sum over levels and points of sum_rs W[r,s] E[r,s] with seeded N(0,1) weights.
+Forward and adjoint solves run to rtol = 1e-11, so the gradients are compared at 1e-8
+relative (per level, in the max norm over elements)."""
+import numpy as np
+import pytest
+
+import mch_inputs as mi
+from oracle import adjoint, plan
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+import paper_2503_01276_gb300 as mch  # noqa: E402
+
+
+def _case(strides, n_fine, macro, precision, name="channel2d_17x17_L3"):
+    wl = mi.small_workload(name, n_fine=n_fine, macro_n=macro, strides=strides,
+                           precision=precision)
+    pl = plan.level_plan(wl)
+    med = [mi.media(wl, l["points"], wl.n_level(k + 1)) for k, l in enumerate(pl)]
+    rng = np.random.default_rng(7)
+    W = [rng.standard_normal((len(l["points"]), wl.n_rhs, wl.n_rhs)) for l in pl]
+    return wl, pl, med, W
+
+
+def _gpu_grad(wl, med, W, device=True):
+    s = mch.Solver.from_workload(wl, rtol=1e-11)
+    Es = []
+    for lev in range(1, wl.n_levels + 1):
+        k, l = med[lev - 1]
+        s.solve_level(lev, torch.from_numpy(k).cuda(), torch.from_numpy(l).cuda())
+        Es.append(s.effective_coeffs(lev))
+    if device:
+        Wd = [torch.from_numpy(w).cuda() for w in W]
+        G = [torch.zeros(m[0].shape, dtype=torch.float64, device="cuda") for m in med]
+        s.backward(Wd, G)
+        G = [g.cpu().numpy() for g in G]
+    else:
+        G = [np.zeros(m[0].shape) for m in med]
+        s.backward(W, G)
+    return Es, G
+
+
+@pytest.mark.parametrize("strides,n_fine,macro,precision", [
+    ((1,), 32, 3, "mixed"),
+    ((2, 1), 32, 3, "mixed"),
+    ((4, 2, 1), 64, 5, "mixed"),
+    ((4, 2, 1), 64, 5, "fp64"),
+])
+def test_gradient_matches_oracle(strides, n_fine, macro, precision):
+    wl, pl, med, W = _case(strides, n_fine, macro, precision)
+    Es, G = _gpu_grad(wl, med, W)
+    fwd = adjoint.forward(wl, pl, med)
+    Go = adjoint.backward(wl, pl, med, fwd, W)
+    for n in range(wl.n_levels):
+        err = np.abs(G[n] - Go[n]).max() / np.abs(Go[n]).max()
+        assert err < 1e-8, (n + 1, err)
+    # Euler identity on the GPU's own loss and gradient
+    Lg = sum(float(np.sum(W[n] * Es[n])) for n in range(wl.n_levels))
+    sk = sum(float(np.sum(med[n][0] * G[n])) for n in range(wl.n_levels))
+    assert abs(sk - Lg) <= 1e-8 * abs(Lg)
+
+
+def test_gradient_host_buffers():
+    wl, pl, med, W = _case((2, 1), 32, 3, "mixed")
+    _, Gd = _gpu_grad(wl, med, W, device=True)
+    _, Gh = _gpu_grad(wl, med, W, device=False)
+    for a, b in zip(Gd, Gh):
+        assert np.abs(a - b).max() <= 1e-9 * np.abs(b).max()
+
+
+def test_three_continua_gradient():
+    wl, pl, med, W = _case((2, 1), 64, 3, "mixed", name="incl2d_33x33_L4")
+    _, G = _gpu_grad(wl, med, W)
+    fwd = adjoint.forward(wl, pl, med)
+    Go = adjoint.backward(wl, pl, med, fwd, W)
+    for n in range(wl.n_levels):
+        err = np.abs(G[n] - Go[n]).max() / np.abs(Go[n]).max()
+        assert err < 1e-8, (n + 1, err)
