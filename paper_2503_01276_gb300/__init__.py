@@ -8,11 +8,14 @@ raises ImportError if it has not been built (``paper_2503_01276_gb300.build.buil
 _EXPORTS = ("MCH_FP64", "MCH_MIXED", "LIB_PATH", "MchDesc", "MchError", "Solver",
             "desc_from_workload", "direct_noalloc", "load_library", "make_desc", "plan_level")
 
-__all__ = list(_EXPORTS)
+__all__ = list(_EXPORTS) + ["homogenize", "HomogenizeFn"]
 
 
 def __getattr__(name):
     if name in _EXPORTS:
         from . import _mch
         return getattr(_mch, name)
+    if name in ("homogenize", "HomogenizeFn"):
+        from . import autograd
+        return getattr(autograd, name)
     raise AttributeError(name)

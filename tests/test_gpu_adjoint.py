@@ -82,3 +82,28 @@ def test_three_continua_gradient():
     for n in range(wl.n_levels):
         err = np.abs(G[n] - Go[n]).max() / np.abs(Go[n]).max()
         assert err < 1e-8, (n + 1, err)
+
+
+def test_autograd_directional_derivative():
+    """loss.backward() through torch.autograd against a central difference of the loss
+    along a random direction (all levels' kappa perturbed together)."""
+    wl, pl, med, W = _case((2, 1), 32, 3, "mixed")
+    s = mch.Solver.from_workload(wl, rtol=1e-11)
+    kap = [torch.from_numpy(m[0]).cuda().requires_grad_(True) for m in med]
+    lab = [torch.from_numpy(m[1]).cuda() for m in med]
+    Wt = [torch.from_numpy(w).cuda() for w in W]
+    Es = mch.homogenize(s, kap, lab)
+    loss = sum((w * e).sum() for w, e in zip(Wt, Es))
+    loss.backward()
+    rng = np.random.default_rng(5)
+    dirs = [torch.from_numpy(rng.standard_normal(m[0].shape)).cuda() * k.detach()
+            for m, k in zip(med, kap)]
+    h = 1e-6
+    vals = []
+    for sgn in (+1, -1):
+        kp = [(k.detach() + sgn * h * dv) for k, dv in zip(kap, dirs)]
+        Ep = mch.homogenize(s, kp, lab)
+        vals.append(float(sum((w * e).sum() for w, e in zip(Wt, Ep))))
+    fd = (vals[0] - vals[1]) / (2 * h)
+    ad = float(sum((k.grad * dv).sum() for k, dv in zip(kap, dirs)))
+    assert abs(fd - ad) <= 1e-5 * abs(ad)
