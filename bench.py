@@ -9,9 +9,14 @@ already resident in device memory. The L2 cache is flushed (a 512 MB device writ
 outside the timed event pairs) before every timed step.
 
 JSON line keys beyond the base contract:
-  roofline      the PCG sweep kernel (the time sink): algorithmic FP32 flops of the
-                iterations it ran / its CUDA-event time, against the FP32 ALU peak derived
-                from 152 SMs x 128 FP32 lanes x 2 flops x the sampled SM clock.
+  roofline      the persistent level kernel k_level2d (the time sink; FP32 PCG sweeps
+                inside FP64 refinement steps, all of a level's points in one launch):
+                algorithmic FP32 flops of the PCG iterations it ran / its CUDA-event time,
+                against the FP32 ALU peak 152 SMs x 128 FP32 lanes x 2 flops x the sampled
+                SM clock. The kernel keeps its whole state in shared memory, so DRAM traffic
+                is small and the bound is the ALU (and the FP64 refinement steps).
+  plain_fp64_per_point  the unbatched comparator: the same workload solved in FP64 with one
+                macropoint per constrained-solve launch (point_batch = 1).
   cpu_baseline  the FP64 oracle (SciPy) on one host core, timed on a sample of points per
                 level and extrapolated to the whole workload.
   e2e           the same step through the public API with pinned host buffers (media
@@ -45,6 +50,13 @@ WORKLOAD = "channel2d_17x17_L3"
 # products 8, x/r/p updates 6, M^-1 r and M^-1 q 2, Ct^T lambda gather 4, two Ct scatters 8
 FLOPS_PER_NODE_ITER = 45
 SMS, FP32_LANES = 152, 128
+# DRAM bytes (read + write) per k_level2d launch of this workload (levels 1, 2, 3), from one
+# ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
+#   python bench.py --steps 1 --warmup 3 --no-cpu --no-plain
+# Valid only for the kernel source it was taken on: the JSON reports null when the
+# sources' hash differs.
+LEVEL_TRAFFIC = {"sha256_16": ("fdbff188de809e3d", "7fb67ff164f56870"),
+                 "bytes_per_launch": (2.83136e6, 20.28083e6, 16.80358e6)}
 
 
 class ClockSampler:
@@ -93,6 +105,34 @@ class ClockSampler:
         return {"sm_mhz": float(np.median(sm)) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
                 "samples": len(self.samples)}
+
+
+def _level_traffic():
+    import hashlib
+    got = []
+    for f in ("k_level.cuh", "k_level_f32.cu"):
+        with open(os.path.join(ROOT, "paper_2503_01276_gb300", "csrc", f), "rb") as fh:
+            got.append(hashlib.sha256(fh.read()).hexdigest()[:16])
+    if tuple(got) != LEVEL_TRAFFIC["sha256_16"]:
+        return None, None
+    b = LEVEL_TRAFFIC["bytes_per_launch"]
+    return float(np.mean(b)), list(b)
+
+
+def max_over_ranks(t_local: float, dist, device) -> float:
+    """Largest of the ranks' timed-region durations (every rank gets it)."""
+    import torch
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(t_local)
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: int, world: int, steps: int, t_max: float) -> float:
+    """Units all ranks processed / the slowest rank's time (weak scaling: every rank solves
+    its own hierarchy of the same size)."""
+    return units_per_rank_step * world * steps / t_max
 
 
 def _peaks():
@@ -156,40 +196,99 @@ def cpu_baseline(wl, Eg_by_level, per_level=2, budget_s=25.0):
 
 
 def run_reference(args, rank, world):
+    """The oracle arm: each step is the bounded oracle sample of the workload (two points per
+    level, timed one by one on one host core, extrapolated to the whole workload)."""
     if rank != 0:
         return
-    wl = mi.workload(WORKLOAD)
-    vals = []
-    for _ in range(args.warmup):
-        pass
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
         env.pop(k, None)
-    for _ in range(args.steps):
+
+    def leg():
         out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-leg", ""],
                              capture_output=True, text=True, env=env, timeout=600)
-        vals.append(json.loads(out.stdout.strip().splitlines()[-1])["cpu"]["value"])
-    v = float(np.mean(vals))
+        return json.loads(out.stdout.strip().splitlines()[-1])["cpu"]
+
+    for _ in range(args.warmup):
+        leg()
+    legs = [leg() for _ in range(args.steps)]
+    v = float(np.mean([c["value"] for c in legs]))
+    wl = mi.workload(WORKLOAD)
+    rhs_per_step = sum(_level_sizes(wl)) * wl.n_rhs
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "RHS/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "macropoints": "17x17", "levels": [9, 72, 208],
-                       "rve_grids": [128, 64, 32], "rhs_per_point": 6, "contrast": 1e4},
+            "ms_per_step": 1e3 * rhs_per_step / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(wl, "fp64"),
             "cpu_baseline": {"value": v, "unit": "RHS/s", "cores": 1, "kind": "oracle",
-                             "sample": "1 point per level per step, extrapolated by level sizes"},
+                             "sample": legs[0]["sample"]},
             "e2e": {"value": v, "unit": "RHS/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _level_sizes(wl):
+    from oracle import plan
+    return [len(l["points"]) for l in plan.level_plan(wl)]
+
+
+def _config(wl, precision):
+    return {"workload": WORKLOAD, "macropoints": f"{wl.macro_n}x{wl.macro_n}",
+            "levels": _level_sizes(wl), "rve_grids": [wl.n_level(k + 1) for k in range(wl.n_levels)],
+            "rhs_per_point": wl.n_rhs, "contrast": wl.contrast, "precision": precision,
+            "l2": "flushed before every timed step (512 MB write, untimed)"}
+
+
+def plain_fp64_leg(wl, med_dev, flush, steps, stream):
+    """The unbatched FP64 comparator: same workload and media, FP64 PCG, one macropoint per
+    constrained-solve launch. Returns RHS/s, ms per step and the largest residual ratio."""
+    import torch
+    import paper_2503_01276_gb300 as mch
+    s = mch.Solver.from_workload(wl, stream=stream.cuda_stream, precision="fp64",
+                                 point_batch=1)
+    L = wl.n_levels
+    E = [torch.zeros((s.num_points(l), s.R, s.R), dtype=torch.float64, device=flush.device)
+         for l in range(1, L + 1)]
+
+    def step():
+        for lev in range(1, L + 1):
+            s.solve_level(lev, *med_dev[lev - 1])
+            s.effective_coeffs(lev, E[lev - 1])
+
+    step()
+    torch.cuda.synchronize()
+    ms = []
+    relres = 0.0
+    launches = 0
+    for _ in range(steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms.append(a.elapsed_time(b))
+        for lev in range(1, L + 1):
+            st = s.stats(lev)
+            relres = max(relres, st["max_relres"])
+            launches += st["pcg_launches"]
+    rhs = sum(s.num_points(l) for l in range(1, L + 1)) * s.R
+    out = {"value": rhs / (np.mean(ms) / 1e3), "unit": "RHS/s", "ms_per_step": float(np.mean(ms)),
+           "steps": steps, "solve_launches_per_step": launches // steps, "max_relres": relres,
+           "kind": "FP64 PCG, one macropoint per constrained-solve launch (point_batch=1)"}
+    s.close()
+    return out, E
 
 
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="mch", choices=["mch", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
+    ap.add_argument("--no-plain", action="store_true",
+                    help="skip the unbatched per-macropoint FP64 comparator")
     ap.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_leg is not None:
@@ -275,17 +374,15 @@ def main():
     if world > 1:
         dist.barrier()
     step_ms = [a.elapsed_time(b) for a, b in evs]
-    t_total = float(np.sum(step_ms)) / 1e3
-    if world > 1:
-        t = torch.tensor([t_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_total = float(t.item())
-    value = rhs_per_step * world * args.steps / t_total
+    t_total = max_over_ranks(float(np.sum(step_ms)) / 1e3, dist if world > 1 else None, dev)
+    value = whole_job_rate(rhs_per_step, world, args.steps, t_total)
 
     # end to end through the public API with pinned host buffers
     e2e_steps = max(3, args.steps // 2)
     step(device_inputs=False)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     tt = 0.0
     for _ in range(e2e_steps):
         flush.zero_()
@@ -294,9 +391,10 @@ def main():
         step(device_inputs=False)
         torch.cuda.synchronize()
         tt += time.perf_counter() - t1
+    tt = max_over_ranks(tt, dist if world > 1 else None, dev)
     h2d = sum(k.numel() * k.element_size() + lb.numel() * lb.element_size() for k, lb in med_host)
     d2h = sum(e.numel() * e.element_size() for e in E_host)
-    e2e_value = rhs_per_step * e2e_steps / tt
+    e2e_value = whole_job_rate(rhs_per_step, world, e2e_steps, tt)
 
     if rank != 0:
         if world > 1:
@@ -308,13 +406,24 @@ def main():
     fp32_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
     pcg_flops = pcg_node_iters * FLOPS_PER_NODE_ITER
     achieved = pcg_flops / (pcg_ms / 1e3) / 1e12 if pcg_ms > 0 else None
-    roofline = {"bound": "alu", "kernel": "k_pcg2d (FP32 PCG sweep)",
+    traffic, traffic_levels = _level_traffic() if args.precision == "mixed" else (None, None)
+    roofline = {"bound": "alu", "kernel": "k_level2d (persistent level solve)",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": (achieved / fp32_peak) if achieved else None, "traffic": None,
+                "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,
+                "traffic_per_launch_by_level": traffic_levels,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x median sampled SM clock",
                 "flops_per_node_iteration": FLOPS_PER_NODE_ITER,
-                "pcg_share_of_step": (pcg_ms / (t_total * 1e3)) if t_total > 0 else None,
-                "pcg_launches": pcg_launches}
+                "kernel_share_of_step": (pcg_ms / (t_total * 1e3)) if t_total > 0 else None,
+                "launches_timed": pcg_launches}
+    plain = None
+    if not args.no_plain:
+        plain, E_plain = plain_fp64_leg(wl, med_dev, flush, 2, stream)
+        plain["speedup_of_value"] = value / world / plain["value"]
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        from util import block_rel_err
+        plain["block_rel_diff_vs_batched"] = max(
+            block_rel_err(a.cpu().numpy(), b.cpu().numpy(), wl.n_cont, wl.dim)
+            for a, b in zip(E_dev, E_plain))
     cpu = None
     acc_err = None
     if not args.no_cpu:
@@ -340,11 +449,8 @@ def main():
             "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "macropoints": "17x17", "levels": [9, 72, 208],
-                       "rve_grids": [128, 64, 32], "rhs_per_point": 6, "contrast": 1e4,
-                       "precision": args.precision, "rhs_per_step": rhs_per_step,
-                       "l2": "flushed before every timed step (512 MB write, untimed)"},
-            "roofline": roofline, "cpu_baseline": cpu,
+            "config": dict(_config(wl, args.precision), rhs_per_step=rhs_per_step),
+            "roofline": roofline, "cpu_baseline": cpu, "plain_fp64_per_point": plain,
             "e2e": {"value": e2e_value, "unit": "RHS/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks,

@@ -78,6 +78,10 @@ typedef struct {
   int max_refine;           /* refinement sweeps (0 -> 6)                                   */
   int keep_parents;         /* 1: keep every level's cell functions on the level-1 grid
                                (needed by mch_backward); 0: keep only what children need    */
+  int point_batch;          /* points per constrained-solve launch: 0 = the whole level in
+                               one persistent launch; k > 0 = at most k points per launch
+                               (1 = one macropoint per launch, the unbatched comparator).
+                               Results do not depend on it                                   */
 } mch_desc;
 
 typedef struct {

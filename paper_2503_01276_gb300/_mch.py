@@ -31,7 +31,8 @@ class MchDesc(C.Structure):
                 ("macro_n", C.c_int), ("level_stride", C.POINTER(C.c_int)), ("n_fine", C.c_int),
                 ("periods", C.c_int), ("overs", C.c_int), ("rve_len", C.c_double),
                 ("precision", C.c_int), ("rtol", C.c_double), ("inner_tol", C.c_double),
-                ("max_iter", C.c_int), ("max_refine", C.c_int), ("keep_parents", C.c_int)]
+                ("max_iter", C.c_int), ("max_refine", C.c_int), ("keep_parents", C.c_int),
+                ("point_batch", C.c_int)]
 
 
 class MchLevelStats(C.Structure):
@@ -95,14 +96,15 @@ def _ptr(a) -> int:
 
 
 def make_desc(dim, n_cont, strides, eta, macro_n, n_fine, periods, rve_len, precision="mixed",
-              rtol=0.0, inner_tol=0.0, max_iter=0, max_refine=0, keep_parents=1, overs=0):
+              rtol=0.0, inner_tol=0.0, max_iter=0, max_refine=0, keep_parents=1, overs=0,
+              point_batch=0):
     arr = (C.c_int * len(strides))(*[int(s) for s in strides])
     d = MchDesc(dim=dim, n_cont=n_cont, n_levels=len(strides), eta=eta, macro_n=macro_n,
                 level_stride=C.cast(arr, C.POINTER(C.c_int)), n_fine=n_fine, periods=periods,
                 overs=overs, rve_len=rve_len,
                 precision=MCH_FP64 if precision == "fp64" else MCH_MIXED, rtol=rtol,
                 inner_tol=inner_tol, max_iter=max_iter, max_refine=max_refine,
-                keep_parents=keep_parents)
+                keep_parents=keep_parents, point_batch=point_batch)
     d._strides_keepalive = arr
     return d
 

@@ -171,7 +171,7 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
   if (d.dim != 2 || d.n_cont < 1 || d.n_cont > MCH_MAX_CONT || d.n_levels < 1 || d.eta < 1 ||
       d.macro_n < 1 || !d.level_stride || d.n_fine < 4 || d.periods < 1 || !(d.rve_len > 0) ||
       (d.precision != MCH_FP64 && d.precision != MCH_MIXED) || d.rtol < 0 || d.inner_tol < 0 ||
-      d.max_iter < 0 || d.max_refine < 0)
+      d.max_iter < 0 || d.max_refine < 0 || d.point_batch < 0)
     return MCH_ERR_ARG;
   if (d.overs != 0) return MCH_ERR_UNSUPPORTED;
   const int nc = d.n_cont * d.periods * d.periods;
@@ -387,22 +387,34 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
     CK(mark(1), "event");
   }
 
-  // ---- constrained solves: one persistent launch (FP64 refinement around inner sweeps)
+  // ---- constrained solves: one persistent launch (FP64 refinement around inner sweeps), or
+  // point_batch points per launch
   const int max_iter = d.max_iter > 0 ? d.max_iter : 4 * L.n + 50;
-  if (fp64) {
-    LevelArgs<double> la{(int)np, R, L.n, P, N, nc, L.nv, ilog2(L.n / P), ilog2(P), L.kappa,
-                         L.labels, L.Sinv64, L.Sinv64, L.minv, g, bvec, L.x, L.iters, L.sweeps,
-                         L.ratio, L.ustat, (float)d.inner_tol, max_iter, d.rtol, d.max_refine,
-                         L.lam};
-    CK(launch_level2d<double>(la, st), "level fp64");
-  } else {
-    LevelArgs<float> la{(int)np, R, L.n, P, N, nc, L.nv, ilog2(L.n / P), ilog2(P), L.kappa,
-                        L.labels, L.Sinv32, L.Sinv64, L.minv, g, bvec, L.x, L.iters, L.sweeps,
-                        L.ratio, L.ustat, (float)d.inner_tol, max_iter, d.rtol, d.max_refine,
-                        L.lam};
-    CK(launch_level2d<float>(la, st), "level fp32");
+  const size_t chunk = d.point_batch > 0 ? std::min(np, (size_t)d.point_batch) : np;
+  int solve_launches = 0;
+  for (size_t p0 = 0; p0 < np; p0 += chunk) {
+    const int cn = (int)std::min(chunk, np - p0);
+    const size_t u0 = p0 * R;
+    const double *bb = bvec ? bvec + u0 * L.nv : nullptr;
+    double *lam = L.lam ? L.lam + u0 * nc : nullptr;
+    if (fp64) {
+      LevelArgs<double> la{cn, R, L.n, P, N, nc, L.nv, ilog2(L.n / P), ilog2(P),
+                           L.kappa + p0 * ne, L.labels + p0 * ne, L.Sinv64 + p0 * nc * nc,
+                           L.Sinv64 + p0 * nc * nc, L.minv + p0 * L.nv, g + p0 * nc * R, bb,
+                           L.x + u0 * L.nv, L.iters + u0, L.sweeps + u0, L.ratio + u0,
+                           L.ustat + u0, (float)d.inner_tol, max_iter, d.rtol, d.max_refine, lam};
+      CK(launch_level2d<double>(la, st), "level fp64");
+    } else {
+      LevelArgs<float> la{cn, R, L.n, P, N, nc, L.nv, ilog2(L.n / P), ilog2(P),
+                          L.kappa + p0 * ne, L.labels + p0 * ne, L.Sinv32 + p0 * nc * nc,
+                          L.Sinv64 + p0 * nc * nc, L.minv + p0 * L.nv, g + p0 * nc * R, bb,
+                          L.x + u0 * L.nv, L.iters + u0, L.sweeps + u0, L.ratio + u0,
+                          L.ustat + u0, (float)d.inner_tol, max_iter, d.rtol, d.max_refine, lam};
+      CK(launch_level2d<float>(la, st), "level fp32");
+    }
+    ++h->launches;
+    ++solve_launches;
   }
-  ++h->launches;
   CK(mark(2), "event");
 
   // ---- effective coefficients and the cell functions on the level-1 grid
@@ -466,7 +478,7 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
     if (!(rr < d.rtol)) notconv = true;
   }
   for (size_t u = 0; u < np * R; ++u) S.sweeps = std::max(S.sweeps, sweeps[u]);
-  S.pcg_launches = 1;
+  S.pcg_launches = solve_launches;
   for (size_t u = 0; u < np * R; ++u)
     S.pcg_node_iters += (long long)iters[u] * (long long)(L.n - 1) * (L.n - 1);
   for (size_t k = 1; k < tags.size(); ++k) {

@@ -94,6 +94,21 @@ def test_host_buffers_match_device_buffers():
     assert st["h2d_bytes"] > 0
 
 
+@pytest.mark.parametrize("point_batch", [1, 7])
+def test_point_batch_matches_whole_level(point_batch):
+    """Solving a level in chunks of point_batch points per launch (1 = the unbatched
+    per-macropoint solve) gives the same coefficients as one launch for the level."""
+    wl = mi.small_workload("channel2d_17x17_L3", n_fine=64, macro_n=5, strides=(4, 2, 1),
+                           precision="fp64")
+    _, Ea = _run_gpu(wl, rtol=1e-11)
+    s, Eb = _run_gpu(wl, rtol=1e-11, point_batch=point_batch)
+    for a, b in zip(Ea, Eb):
+        assert block_rel_err(a, b, wl.n_cont, wl.dim) < 1e-10
+    np_l = [s.num_points(l) for l in range(1, wl.n_levels + 1)]
+    assert [s.stats(l)["pcg_launches"] for l in range(1, wl.n_levels + 1)] == \
+        [-(-n // point_batch) for n in np_l]
+
+
 def test_full_size_17x17_sampled():
     """The benchmark workload (17x17 points, RVE grids 128/64/32, mixed precision) solved in
     full on the GPU; sampled points of every level checked against the oracle, which
