@@ -51,56 +51,92 @@ def loss(fwd, weights):
                      for i, r in enumerate(lev)))
 
 
-def backward(wl, plan, media_levels, fwd, weights):
-    """dL/dkappa per level, [npts, n_n^d], for L = sum W * E."""
+def _point_adjoint(wl, ops, kap, lab, r, W, V):
+    """One point of level n (ops) in the reverse sweep: its kappa gradient per level-n element
+    and, for n > 1, the seed U pushed to its parents (None at level 1)."""
     d, R = wl.dim, wl.n_rhs
     vol = wl.rve_len ** d
     Kh, _ = fe.unit_element_matrices(d)
+    gf, P = ops.gf, ops.P
+    What = (W + W.T) / vol
+    kf = cell.prolong_medium(kap, d, ops.n_c, ops.rho)
+    lf = cell.prolong_medium(lab, d, ops.n_c, ops.rho)
+    A1 = fe.stiffness_full(gf, kf)
+    C1 = fe.constraint_rows(gf, lf, wl.n_cont, wl.periods)[r["keep"]]
+    AX = (P.T @ A1 @ P).tocsr()
+    CX = (C1 @ P).tocsr()
+    Phi = r["Phi"].T                                   # [nodes, R]
+    f = P.T @ V
+    if np.any(f):
+        mu, nu_neg = cell.saddle_solve(AX, CX, f, np.zeros((CX.shape[0], R)))
+        nu = -nu_neg                                   # A mu + C^T nu = f
+    else:
+        mu = np.zeros((P.shape[1], R))
+        nu = np.zeros((CX.shape[0], R))
+    Pmu = P @ mu
+    # kappa gradient per fine element, summed over the fine elements of each E
+    Pe = Phi[gf.enodes]                                # [ne, 2^d, R]
+    Me = Pmu[gf.enodes]
+    KP = np.einsum("ab,ebr->ear", Kh, Pe)              # Khat Phi on each element
+    ge = (np.einsum("rs,ear,eas->e", W / vol, Pe, KP) -
+          np.einsum("ear,ear->e", Me, KP)) * gf.h ** (d - 2)
+    ec = gf.ecoord // ops.rho
+    idx = sum(ec[:, a] * ops.n_c ** a for a in range(d))
+    g = np.bincount(idx, weights=ge, minlength=ops.n_c ** d)
+    if ops.level == 1:
+        return g, None
+    beta = r["beta"]
+    U = V + (A1 @ Phi - C1.T @ beta) @ What.T - A1 @ Pmu - C1.T @ nu
+    U[~np.isin(np.arange(gf.n_nodes), gf.interior_nodes)] = 0.0
+    return g, U
+
+
+def backward(wl, plan, media_levels, fwd, weights):
+    """dL/dkappa per level, [npts, n_n^d], for L = sum W * E."""
+    R = wl.n_rhs
     L = len(plan)
-    nf_nodes = fe.Grid(d, wl.n_fine, wl.rve_len).n_nodes
+    nf_nodes = fe.Grid(wl.dim, wl.n_fine, wl.rve_len).n_nodes
     seeds = [np.zeros((len(plan[n]["points"]), nf_nodes, R)) for n in range(L)]
     grads = [None] * L
     for n in range(L - 1, -1, -1):
         ops = cell.LevelOps(wl, n + 1)
-        gf, P = ops.gf, ops.P
         kap, lab = media_levels[n]
         npts = len(plan[n]["points"])
-        g_lev = np.zeros((npts, ops.n_c ** d))
+        g_lev = np.zeros((npts, ops.n_c ** wl.dim))
         for i in range(npts):
-            r = fwd[n][i]
-            W = weights[n][i]
-            What = (W + W.T) / vol
-            kf = cell.prolong_medium(kap[i], d, ops.n_c, ops.rho)
-            lf = cell.prolong_medium(lab[i], d, ops.n_c, ops.rho)
-            A1 = fe.stiffness_full(gf, kf)
-            C1 = fe.constraint_rows(gf, lf, wl.n_cont, wl.periods)[r["keep"]]
-            AX = (P.T @ A1 @ P).tocsr()
-            CX = (C1 @ P).tocsr()
-            Phi = r["Phi"].T                                   # [nodes, R]
-            V = seeds[n][i]
-            f = P.T @ V
-            if np.any(f):
-                mu, nu_neg = cell.saddle_solve(AX, CX, f, np.zeros((CX.shape[0], R)))
-                nu = -nu_neg                                   # A mu + C^T nu = f
-            else:
-                mu = np.zeros((P.shape[1], R))
-                nu = np.zeros((CX.shape[0], R))
-            Pmu = P @ mu
-            # kappa gradient per fine element, summed over the fine elements of each E
-            Pe = Phi[gf.enodes]                                # [ne, 2^d, R]
-            Me = Pmu[gf.enodes]
-            KP = np.einsum("ab,ebr->ear", Kh, Pe)              # Khat Phi on each element
-            ge = (np.einsum("rs,ear,eas->e", W / vol, Pe, KP) -
-                  np.einsum("ear,ear->e", Me, KP)) * gf.h ** (d - 2)
-            rho = ops.rho
-            ec = gf.ecoord // rho
-            idx = sum(ec[:, a] * ops.n_c ** a for a in range(d))
-            g_lev[i] = np.bincount(idx, weights=ge, minlength=ops.n_c ** d)
+            g_lev[i], U = _point_adjoint(wl, ops, kap[i], lab[i], fwd[n][i], weights[n][i],
+                                         seeds[n][i])
             if n > 0:
-                beta = r["beta"]
-                U = V + (A1 @ Phi - C1.T @ beta) @ What.T - A1 @ Pmu - C1.T @ nu
-                U[~np.isin(np.arange(gf.n_nodes), gf.interior_nodes)] = 0.0
                 for (lv, pos, w) in plan[n]["parents"][i]:
                     seeds[lv - 1][pos] += w * U
         grads[n] = g_lev
     return grads
+
+
+def backward_sampled(wl, plan, media_fn, weights):
+    """The same gradient for a loss whose weights vanish outside a few points.
+
+    weights: {(level, position): W [R, R]}. Only those points and their ancestors carry
+    seeds, so the forward and reverse sweeps run over that closure alone (Algorithm 1
+    restricted to it). media_fn(level, positions) -> (kappa, labels). Returns
+    ({(level, position): dL/dkappa [n_n^d]}, loss)."""
+    R = wl.n_rhs
+    fwd = cell.run_sampled(wl, plan, media_fn, list(weights))
+    nf_nodes = fe.Grid(wl.dim, wl.n_fine, wl.rve_len).n_nodes
+    seeds = {k: np.zeros((nf_nodes, R)) for k in fwd}
+    zero = np.zeros((R, R))
+    loss_val = float(sum(np.sum(W * fwd[k]["E"]) for k, W in weights.items()))
+    grads = {}
+    for n in range(len(plan), 0, -1):
+        pos = sorted(i for (l, i) in fwd if l == n)
+        if not pos:
+            continue
+        ops = cell.LevelOps(wl, n)
+        kap, lab = media_fn(n, pos)
+        for k, i in enumerate(pos):
+            grads[(n, i)], U = _point_adjoint(wl, ops, kap[k], lab[k], fwd[(n, i)],
+                                              weights.get((n, i), zero), seeds[(n, i)])
+            if n > 1:
+                for (lv, pp, w) in plan[n - 1]["parents"][i]:
+                    seeds[(lv, pp)] += w * U
+    return grads, loss_val

@@ -60,3 +60,33 @@ def test_central_differences(strides, n_fine, macro):
             assert abs(fd - g[n][i, e]) <= 1e-5 * scale + 1e-9 * abs(out[0]) / h, (n, i, e, fd, g[n][i, e])
             checked += 1
     assert checked == 3 * len(pl)
+
+
+def test_sampled_backward_matches_full_backward():
+    """The closure-restricted reverse sweep (weights on two points only) reproduces the full
+    sweep's gradient on every point of the closure and zero elsewhere."""
+    wl = mi.small_workload("channel2d_17x17_L3", n_fine=32, macro_n=5, strides=(4, 2, 1),
+                           precision="fp64")
+    pl = plan.level_plan(wl)
+    med = [mi.media(wl, l["points"], wl.n_level(k + 1)) for k, l in enumerate(pl)]
+    rng = np.random.default_rng(3)
+    R = wl.n_rhs
+    picks = {(3, 5): rng.standard_normal((R, R)), (2, 1): rng.standard_normal((R, R))}
+    W = [np.zeros((len(l["points"]), R, R)) for l in pl]
+    for (lv, i), w in picks.items():
+        W[lv - 1][i] = w
+    fwd = adjoint.forward(wl, pl, med)
+    full = adjoint.backward(wl, pl, med, fwd, W)
+
+    def media_fn(lv, pos):
+        return mi.media(wl, pl[lv - 1]["points"][pos], wl.n_level(lv))
+
+    samp, loss_s = adjoint.backward_sampled(wl, pl, media_fn, picks)
+    assert abs(loss_s - adjoint.loss(fwd, W)) <= 1e-12 * abs(loss_s)
+    for lv in range(1, 4):
+        for i in range(len(pl[lv - 1]["points"])):
+            g = full[lv - 1][i]
+            if (lv, i) in samp:
+                assert np.abs(samp[(lv, i)] - g).max() <= 1e-10 * np.abs(g).max()
+            else:
+                assert not np.any(g)
