@@ -77,7 +77,12 @@ typedef struct {
   int max_iter;             /* PCG iterations per sweep (0 -> 4 n_level + 50)               */
   int max_refine;           /* refinement sweeps (0 -> 6)                                   */
   int keep_parents;         /* 1: keep every level's cell functions on the level-1 grid
-                               (needed by mch_backward); 0: keep only what children need    */
+                               after the forward pass (checkpoint for mch_backward);
+                               0: free them once the last level is solved and after
+                               mch_backward, and recompute them from the stored level-grid
+                               solutions (interpolation + prolongation, no new solve) when
+                               mch_backward, mch_cell_functions or a later mch_solve_level
+                               needs them                                                   */
   int point_batch;          /* points per constrained-solve launch: 0 = the whole level in
                                one persistent launch; k > 0 = at most k points per launch
                                (1 = one macropoint per launch, the unbatched comparator).

@@ -57,6 +57,7 @@ struct mch_handle {
   double *yfine = nullptr, *yc = nullptr;
   // backward-pass buffers, allocated on the first mch_backward
   bool bw_ready = false;
+  bool phi_released = false;  // keep_parents = 0: level-1-grid cell functions freed
   double *psi1 = nullptr, *psi2 = nullptr, *lamadj = nullptr, *gzero = nullptr, *Wd = nullptr,
          *dk = nullptr, *bw_ratio = nullptr;
   int *bw_iters = nullptr, *bw_sweeps = nullptr, *bw_status = nullptr;
@@ -130,6 +131,78 @@ int ilog2(int v) {
 
 bool valid_level(const mch_handle *h, int level) {
   return h && level >= 1 && level <= (int)h->lv.size();
+}
+
+void dfree(mch_handle *h, void *p) {
+  if (!p) return;
+  for (size_t i = 0; i < h->allocs.size(); ++i)
+    if (h->allocs[i] == p) {
+      h->allocs.erase(h->allocs.begin() + i);
+      break;
+    }
+  cudaFree(p);
+}
+
+// Interpolation and correction data of a child level on the level-1 grid (Phi = I, A_1 I,
+// g -= C_1 I); g holds the targets on entry.
+cudaError_t launch_child(mch_handle *h, Level &L, double *g) {
+  const mch_desc &d = h->d;
+  ChildArgs ca{L.npts, h->R, d.n_fine, ilog2(L.rho), L.nvf, h->slots, ilog2(d.n_fine / d.periods),
+               ilog2(d.periods), d.n_cont, h->nc, L.par_ptr, L.par_w, L.kappa, L.labels, L.phi,
+               h->yfine, g, 1.0 / ((double)L.rho * L.rho)};
+  return launch_child_fine2d(ca, h->st);
+}
+
+// keep_parents = 0: frees every level's cell functions on the level-1 grid.
+cudaError_t release_phi(mch_handle *h) {
+  cudaError_t e = cudaStreamSynchronize(h->st);
+  if (e != cudaSuccess) return e;
+  for (Level &L : h->lv) {
+    dfree(h, L.phi);
+    L.phi = nullptr;
+  }
+  h->phi_released = true;
+  return cudaSuccess;
+}
+
+// Reallocates the cell functions and recomputes those of every solved level from its stored
+// level-grid solution, levels in order (Phi = Xi at level 1, Phi = I + P Xi above): the
+// same kernels as the forward pass, without a new solve.
+cudaError_t restore_phi(mch_handle *h) {
+  if (!h->phi_released) return cudaSuccess;
+  const int R = h->R;
+  for (Level &L : h->lv) {
+    cudaError_t e = dalloc(h, &L.phi, (size_t)L.npts * R * L.nvf);
+    if (e != cudaSuccess) return e;
+  }
+  for (size_t l = 1; l < h->lv.size(); ++l) {
+    Level &L = h->lv[l];
+    std::vector<const double *> hp((size_t)L.npts * h->slots, nullptr);
+    for (size_t i = 0; i < hp.size(); ++i) {
+      const int pl = L.plan.par_level[i];
+      if (pl > 0) hp[i] = h->lv[pl - 1].phi + (size_t)L.plan.par_pos[i] * R * L.nvf;
+    }
+    cudaError_t e = cudaMemcpyAsync(const_cast<const double **>(L.par_ptr), hp.data(),
+                                    hp.size() * sizeof(void *), cudaMemcpyHostToDevice, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) return e;
+  }
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    Level &L = h->lv[l];
+    if (!L.solved) continue;
+    cudaError_t e;
+    if (l == 0) {
+      e = cudaMemcpyAsync(L.phi, L.x, (size_t)L.npts * R * L.nv * sizeof(double),
+                          cudaMemcpyDeviceToDevice, h->st);
+    } else {
+      e = launch_child(h, L, L.gI);
+      if (e == cudaSuccess)
+        e = launch_prolong_add2d(L.npts, R, h->d.n_fine, L.rho, L.x, L.nv, L.phi, L.nvf, h->st);
+    }
+    if (e != cudaSuccess) return e;
+  }
+  h->phi_released = false;
+  return cudaStreamSynchronize(h->st);
 }
 
 }  // namespace
@@ -337,6 +410,7 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
     if (!h->lv[k].solved)
       return set_err(h, MCH_ERR_ORDER, "level " + std::to_string(level) +
                                            " needs level " + std::to_string(k + 1) + " first");
+  CK(restore_phi(h), "recompute cell functions");
   Level &L = h->lv[li];
   const mch_desc &d = h->d;
   const int R = h->R, nc = h->nc, N = d.n_cont, P = d.periods;
@@ -374,10 +448,7 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
     CK(cudaMemcpyAsync(L.gI, L.G, np * nc * R * sizeof(double), cudaMemcpyDeviceToDevice, st),
        "targets copy");
     CK(cudaMemsetAsync(L.E, 0, np * R * R * sizeof(double), st), "zero E");
-    ChildArgs ca{(int)np, R, d.n_fine, ilog2(L.rho), L.nvf, h->slots, ilog2(d.n_fine / P),
-                 ilog2(P), N, nc, L.par_ptr, L.par_w, L.kappa, L.labels, L.phi, h->yfine,
-                 L.gI, 1.0 / ((double)L.rho * L.rho)};
-    CK(launch_child_fine2d(ca, st), "child fine");
+    CK(launch_child(h, L, L.gI), "child fine");
     CK(launch_gram((int)np, R, L.nvf, L.phi, h->yfine, inv_vol, L.E, st), "gram I");
     CK(launch_restrict2d((int)np, R, d.n_fine, L.rho, h->yfine, L.nvf, -1.0, L.b, L.nv, st),
        "restrict");
@@ -501,6 +572,7 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
                        std::to_string(pstat[bad_pt]) +
                        " (1 kappa<=0, 2 label>=n_cont, 4 singular constraints, 8 absent continuum)");
   L.solved = true;
+  if (!d.keep_parents && li == d.n_levels - 1) CK(release_phi(h), "release cell functions");
   if (breakdown)
     return set_err(h, MCH_ERR_BREAKDOWN, "PCG breakdown at unit " + std::to_string(bad_unit));
   if (notconv) {
@@ -531,6 +603,7 @@ mch_status mch_cell_functions(mch_handle *h, int level, double *phi) {
   if (!valid_level(h, level) || !phi) return set_err(h, MCH_ERR_ARG, "bad argument");
   Level &L = h->lv[level - 1];
   if (!L.solved) return set_err(h, MCH_ERR_ORDER, "level not solved");
+  CK(restore_phi(h), "recompute cell functions");
   // library vectors are padded to nvf entries; the caller's layout is dense (n_fine+1)^2
   const size_t row = (size_t)(h->d.n_fine + 1) * (h->d.n_fine + 1) * sizeof(double);
   const size_t rows = (size_t)L.npts * h->R;
@@ -573,6 +646,7 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
   }
   cudaStream_t st = h->st;
   const int nvf = nv_of(d.n_fine);
+  CK(restore_phi(h), "recompute cell functions");
   if (!h->bw_ready) {
     size_t mfine = 0, munit = 0, mnc = 0, mrr = 0, mel = 0;
     for (int l = 0; l < Lv; ++l) {
@@ -678,6 +752,7 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
     }
   }
   CK(cudaStreamSynchronize(st), "backward sync");
+  if (!d.keep_parents) CK(release_phi(h), "release cell functions");
   if (breakdown) return set_err(h, MCH_ERR_BREAKDOWN, "adjoint PCG breakdown");
   if (!(worst < d.rtol)) {
     char buf[128];

@@ -130,6 +130,32 @@ def test_full_size_17x17_sampled():
         assert st["max_relres"] < 1e-8
 
 
+def test_full_size_33x33_three_continua_sampled():
+    """Four levels (25/56/208/800 points on RVE grids 256/128/64/32), three continua
+    (channels at contrast 1e6, lognormal inclusions, matrix), nine cell functions per
+    point, mixed precision at the default tolerance: sampled points of every level, including
+    points with two and with four parents, against the oracle."""
+    wl = mi.workload("incl2d_33x33_L4")
+    s, Eg = _run_gpu(wl)
+    pl = plan.level_plan(wl)
+    targets = [(1, 12), (2, 30)]
+    for lv in (3, 4):
+        par = pl[lv - 1]["parents"]
+        two = next(i for i in range(len(par)) if len(par[i]) == 2)
+        four = next(i for i in range(len(par) - 1, -1, -1) if len(par[i]) == 4)
+        targets += [(lv, two), (lv, four)]
+
+    def media_fn(lv, pos):
+        return mi.media(wl, pl[lv - 1]["points"][pos], wl.n_level(lv))
+
+    ref = cell.run_sampled(wl, pl, media_fn, targets)
+    for (lv, i) in targets:
+        err = block_rel_err(Eg[lv - 1][i], ref[(lv, i)]["E"], wl.n_cont, wl.dim)
+        assert err < 1e-6, (lv, i, err)
+    for lev in range(1, 5):
+        assert s.stats(lev)["max_relres"] < 1e-8
+
+
 def test_level_order_error():
     wl = mi.small_workload("channel2d_17x17_L3", n_fine=32, macro_n=5, strides=(2, 1))
     s = mch.Solver.from_workload(wl)
