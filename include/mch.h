@@ -69,10 +69,14 @@ typedef struct {
   int overs;                /* oversampling layers o; only 0 is built (MCH_ERR_UNSUPPORTED) */
   double rve_len;           /* l: RVE side length                                           */
   int precision;            /* MCH_MIXED (FP32 PCG inside FP64 refinement) or MCH_FP64      */
-  double rtol;              /* stop when sqrt(r'M^-1 r / r0'M^-1 r0) < rtol for the FP64
-                               projected residual (0 -> 1e-8). A child's coefficients inherit
-                               the error of its parents' functions to first order (about
-                               rtol); a level's own coefficients are quadratic in its error */
+  double rtol;              /* stop when sqrt(r'M^-1 r / rho_ref) < rtol for the FP64
+                               projected residual r (0 -> 1e-8), with rho_ref the larger of
+                               the first step's r'M^-1 r and b'M^-1 b, b the right-hand side
+                               of a correction problem (n > 1), so the test bounds the error
+                               of the cell function I + P Xi relative to its own scale. A
+                               child's coefficients inherit the error of its parents'
+                               functions to first order (about rtol); a level's own
+                               coefficients are quadratic in its error */
   double inner_tol;         /* per-sweep PCG reduction of the same norm (0 -> 1e-4)         */
   int max_iter;             /* PCG iterations per sweep (0 -> 4 n_level + 50)               */
   int max_refine;           /* refinement sweeps (0 -> 6)                                   */

@@ -18,6 +18,7 @@
 
 #include "../../include/mch.h"
 #include "common.cuh"
+#include "k3d.cuh"
 #include "kernels.h"
 #include "plan.h"
 
@@ -32,6 +33,7 @@ struct Level {
   uint8_t *labels = nullptr;
   double *G = nullptr, *gI = nullptr, *Sinv64 = nullptr, *Sacc = nullptr, *bacc = nullptr;
   float *Sinv32 = nullptr;
+  float *kap32 = nullptr, *minv32 = nullptr;  // 3D mixed precision: FP32 copies
   double *x = nullptr, *b = nullptr, *minv = nullptr;
   double *ratio = nullptr;
   int *iters = nullptr, *sweeps = nullptr, *ustat = nullptr, *pstat = nullptr, *dropped = nullptr;
@@ -55,6 +57,12 @@ struct mch_handle {
   std::vector<Level> lv;
   // scratch shared by the levels (solved one after another)
   double *yfine = nullptr, *yc = nullptr;
+  double *bnorm = nullptr;  // [unit] b'M^-1 b of the current correction or adjoint problem
+  // 3D level-solve scratch: inner vectors, FP64 residual, rotating accumulators, counters
+  void *s3p = nullptr, *s3r = nullptr, *s3d = nullptr, *s3q = nullptr;
+  double *s3r64 = nullptr, *s3acc = nullptr;
+  int *s3cnt = nullptr;
+  size_t s3_units_nv = 0, s3_acc = 0;
   // backward-pass buffers, allocated on the first mch_backward
   bool bw_ready = false;
   bool phi_released = false;  // keep_parents = 0: level-1-grid cell functions freed
@@ -129,6 +137,14 @@ int ilog2(int v) {
   return r;
 }
 
+int nvd(int dim, int n) { return dim == 3 ? nv3_of(n) : nv_of(n); }
+size_t elems(int dim, int n) { return dim == 3 ? (size_t)n * n * n : (size_t)n * n; }
+
+bool level3d_supported(int n, int P) {
+  const int m = P > 0 ? n / P : 0;
+  return n >= 4 && P >= 1 && n % P == 0 && m >= 2 && (m & (m - 1)) == 0 && (n & (n - 1)) == 0;
+}
+
 bool valid_level(const mch_handle *h, int level) {
   return h && level >= 1 && level <= (int)h->lv.size();
 }
@@ -143,14 +159,105 @@ void dfree(mch_handle *h, void *p) {
   cudaFree(p);
 }
 
+double rho_pow(const mch_handle *h, int rho) {
+  return h->d.dim == 3 ? (double)rho * rho * rho : (double)rho * rho;
+}
+
 // Interpolation and correction data of a child level on the level-1 grid (Phi = I, A_1 I,
-// g -= C_1 I); g holds the targets on entry.
-cudaError_t launch_child(mch_handle *h, Level &L, double *g) {
+// g -= C_1 I); g holds the targets on entry. Returns the number of kernels launched via
+// *nl.
+cudaError_t launch_child(mch_handle *h, Level &L, double *g, int *nl = nullptr) {
   const mch_desc &d = h->d;
   ChildArgs ca{L.npts, h->R, d.n_fine, ilog2(L.rho), L.nvf, h->slots, ilog2(d.n_fine / d.periods),
                ilog2(d.periods), d.n_cont, h->nc, L.par_ptr, L.par_w, L.kappa, L.labels, L.phi,
-               h->yfine, g, 1.0 / ((double)L.rho * L.rho)};
-  return launch_child_fine2d(ca, h->st);
+               h->yfine, g, 1.0 / rho_pow(h, L.rho)};
+  if (d.dim == 2) {
+    if (nl) *nl = 1;
+    return launch_child_fine2d(ca, h->st);
+  }
+  if (nl) *nl = 2;
+  cudaError_t e = launch_interp3d(ca, h->st);
+  if (e != cudaSuccess) return e;
+  return launch_fine_apply3d(ca, d.rve_len / d.n_fine, h->st);
+}
+
+cudaError_t launch_prolong(mch_handle *h, Level &L) {
+  if (h->d.dim == 2)
+    return launch_prolong_add2d(L.npts, h->R, h->d.n_fine, L.rho, L.x, L.nv, L.phi, L.nvf, h->st);
+  return launch_prolong_add3d(L.npts, h->R, h->d.n_fine, L.rho, L.x, L.nv, L.phi, L.nvf, h->st);
+}
+
+cudaError_t launch_restrict(mch_handle *h, Level &L, const double *yf, double scale, double *out) {
+  if (h->d.dim == 2)
+    return launch_restrict2d(L.npts, h->R, h->d.n_fine, L.rho, yf, L.nvf, scale, out, L.nv, h->st);
+  return launch_restrict3d(L.npts, h->R, h->d.n_fine, L.rho, yf, L.nvf, scale, out, L.nv, h->st);
+}
+
+// grows the 3D level-solve scratch to `units_nv` node entries per vector and `acc` doubles
+cudaError_t ensure_s3(mch_handle *h, size_t units_nv, size_t acc) {
+  const size_t tsz = h->d.precision == MCH_FP64 ? sizeof(double) : sizeof(float);
+  if (units_nv > h->s3_units_nv) {
+    for (void **p : {&h->s3p, &h->s3r, &h->s3d, &h->s3q}) {
+      dfree(h, *p);
+      *p = nullptr;
+      unsigned char *q = nullptr;
+      cudaError_t e = dalloc(h, &q, units_nv * tsz);
+      if (e != cudaSuccess) return e;
+      *p = q;
+    }
+    dfree(h, h->s3r64);
+    h->s3r64 = nullptr;
+    cudaError_t e = dalloc(h, &h->s3r64, units_nv);
+    if (e != cudaSuccess) return e;
+    h->s3_units_nv = units_nv;
+  }
+  if (acc > h->s3_acc) {
+    dfree(h, h->s3acc);
+    h->s3acc = nullptr;
+    cudaError_t e = dalloc(h, &h->s3acc, acc);
+    if (e != cudaSuccess) return e;
+    h->s3_acc = acc;
+  }
+  if (!h->s3cnt) return dalloc(h, &h->s3cnt, 4);
+  return cudaSuccess;
+}
+
+// 3D constrained solves of a level (one cooperative launch); x is overwritten.
+cudaError_t solve3d(mch_handle *h, Level &L, const double *g, const double *b, double *x,
+                    int *iters, int *sweeps, double *ratio, int *ustat, double *lam,
+                    const double *bnorm) {
+  const mch_desc &d = h->d;
+  const int R = h->R, nc = h->nc;
+  const size_t units = (size_t)L.npts * R, un = units * L.nv;
+  const size_t acc = 3 * units * (8 + 2 * (size_t)nc);
+  const bool fp64 = d.precision == MCH_FP64;
+  const size_t tsz = fp64 ? sizeof(double) : sizeof(float);
+  cudaError_t e = ensure_s3(h, un, acc);
+  if (e != cudaSuccess) return e;
+  cudaStream_t st = h->st;
+  if ((e = cudaMemsetAsync(x, 0, un * sizeof(double), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(h->s3d, 0, un * tsz, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(h->s3p, 0, un * tsz, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(h->s3acc, 0, acc * sizeof(double), st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(h->s3cnt, 0, 4 * sizeof(int), st)) != cudaSuccess) return e;
+  const int max_iter = d.max_iter > 0 ? d.max_iter : 4 * L.n + 50;
+  const double hn = d.rve_len / L.n;
+  if (fp64) {
+    Level3Args<double> a{L.npts, R, L.n, d.periods, d.n_cont, nc, L.nv, L.n / d.periods,
+                         L.kappa, L.kappa, L.labels, L.Sinv64, L.Sinv64, L.minv, L.minv, g, b, x,
+                         h->s3r64, (double *)h->s3p, (double *)h->s3r, (double *)h->s3d,
+                         (double *)h->s3q, h->s3acc, h->s3cnt, iters, sweeps, ratio, ustat,
+                         (float)d.inner_tol, max_iter, d.rtol, d.max_refine, lam, hn, 0, 0,
+                         bnorm};
+    return launch_level3d<double>(a, st);
+  }
+  Level3Args<float> a{L.npts, R, L.n, d.periods, d.n_cont, nc, L.nv, L.n / d.periods,
+                      L.kappa, L.kap32, L.labels, L.Sinv32, L.Sinv64, L.minv, L.minv32, g, b, x,
+                      h->s3r64, (float *)h->s3p, (float *)h->s3r, (float *)h->s3d,
+                      (float *)h->s3q, h->s3acc, h->s3cnt, iters, sweeps, ratio, ustat,
+                      (float)d.inner_tol, max_iter, d.rtol, d.max_refine, lam, hn, 0, 0,
+                      bnorm};
+  return launch_level3d<float>(a, st);
 }
 
 // keep_parents = 0: frees every level's cell functions on the level-1 grid.
@@ -196,8 +303,7 @@ cudaError_t restore_phi(mch_handle *h) {
                           cudaMemcpyDeviceToDevice, h->st);
     } else {
       e = launch_child(h, L, L.gI);
-      if (e == cudaSuccess)
-        e = launch_prolong_add2d(L.npts, R, h->d.n_fine, L.rho, L.x, L.nv, L.phi, L.nvf, h->st);
+      if (e == cudaSuccess) e = launch_prolong(h, L);
     }
     if (e != cudaSuccess) return e;
   }
@@ -240,15 +346,17 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
   *out = nullptr;
   if (!desc) return MCH_ERR_ARG;
   const mch_desc &d = *desc;
-  if (d.dim == 3) return MCH_ERR_UNSUPPORTED;
-  if (d.dim != 2 || d.n_cont < 1 || d.n_cont > MCH_MAX_CONT || d.n_levels < 1 || d.eta < 1 ||
+  if ((d.dim != 2 && d.dim != 3) || d.n_cont < 1 || d.n_cont > MCH_MAX_CONT || d.n_levels < 1 || d.eta < 1 ||
       d.macro_n < 1 || !d.level_stride || d.n_fine < 4 || d.periods < 1 || !(d.rve_len > 0) ||
       (d.precision != MCH_FP64 && d.precision != MCH_MIXED) || d.rtol < 0 || d.inner_tol < 0 ||
       d.max_iter < 0 || d.max_refine < 0 || d.point_batch < 0)
     return MCH_ERR_ARG;
   if (d.overs != 0) return MCH_ERR_UNSUPPORTED;
-  const int nc = d.n_cont * d.periods * d.periods;
-  if (nc > MCH_MAX_NC) return MCH_ERR_UNSUPPORTED;
+  const int nq = d.dim == 3 ? d.periods * d.periods * d.periods : d.periods * d.periods;
+  const int nc = d.n_cont * nq;
+  if (nc > (d.dim == 3 ? MCH_MAX_NC3 : MCH_MAX_NC)) return MCH_ERR_UNSUPPORTED;
+  // 3D: the Gram and backward kernels take up to 12 cell functions (n_cont <= 3)
+  if (d.dim == 3 && d.n_cont > 3) return MCH_ERR_UNSUPPORTED;
 
   mch_handle *h = new mch_handle();
   h->d = d;
@@ -259,7 +367,7 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
   if (h->d.max_refine == 0) h->d.max_refine = 6;
   h->st = (cudaStream_t)cuda_stream;
   h->R = d.n_cont * (1 + d.dim);
-  h->nq = d.periods * d.periods;
+  h->nq = nq;
   h->nc = nc;
   h->slots = 1 << d.dim;
 
@@ -274,7 +382,9 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
   for (int l = 0; l < d.n_levels; ++l) {
     if (d.n_fine % scale) { delete h; return MCH_ERR_ARG; }
     const int n = d.n_fine / scale;
-    if (!level2d_supported(n, d.periods, d.precision == MCH_FP64)) {
+    const bool ok = d.dim == 2 ? level2d_supported(n, d.periods, d.precision == MCH_FP64)
+                               : level3d_supported(n, d.periods);
+    if (!ok) {
       delete h;
       return MCH_ERR_UNSUPPORTED;
     }
@@ -283,14 +393,14 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
 
   h->lv.resize(d.n_levels);
   size_t max_unit_nv = 0, max_fine = 0, max_unit_nvc = 0;
-  const int nvf = nv_of(d.n_fine);
+  const int nvf = nvd(d.dim, d.n_fine);
   for (int l = 0; l < d.n_levels; ++l) {
     Level &L = h->lv[l];
     L.plan = plans[l];
     L.n = L.plan.n_elem;
     L.rho = d.n_fine / L.n;
     L.npts = (int)L.plan.points.size() / d.dim;
-    L.nv = nv_of(L.n);
+    L.nv = nvd(d.dim, L.n);
     L.nvf = nvf;
     max_unit_nv = std::max(max_unit_nv, (size_t)L.npts * h->R * L.nv);
     max_unit_nvc = std::max(max_unit_nvc, (size_t)L.npts * h->R * L.nv);
@@ -306,15 +416,19 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
   } while (0)
   for (int l = 0; l < d.n_levels; ++l) {
     Level &L = h->lv[l];
-    const size_t np = L.npts, R = h->R, ne = (size_t)L.n * L.n;
+    const size_t np = L.npts, R = h->R, ne = elems(d.dim, L.n);
     ALLOC(L.kappa, np * ne);
     ALLOC(L.labels, np * ne);
     ALLOC(L.G, np * nc * R);
     ALLOC(L.gI, np * nc * R);
     ALLOC(L.Sinv64, np * nc * nc);
     ALLOC(L.Sacc, np * nc * nc);
-    ALLOC(L.bacc, np * nc * 3);
+    ALLOC(L.bacc, np * nc * (d.dim + 1));
     if (d.precision == MCH_MIXED) ALLOC(L.Sinv32, np * nc * nc);
+    if (d.dim == 3 && d.precision == MCH_MIXED) {
+      ALLOC(L.kap32, np * ne);
+      ALLOC(L.minv32, np * L.nv);
+    }
     ALLOC(L.x, np * R * L.nv);
     ALLOC(L.minv, np * L.nv);
     ALLOC(L.b, np * R * L.nv);
@@ -346,6 +460,11 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
     }
   }
   ALLOC(h->yc, max_unit_nvc);
+  {
+    size_t max_units = 0;
+    for (const Level &L : h->lv) max_units = std::max(max_units, (size_t)L.npts * h->R);
+    ALLOC(h->bnorm, max_units);
+  }
   if (max_fine) ALLOC(h->yfine, max_fine);
 #undef ALLOC
   cudaError_t e = cudaStreamSynchronize(h->st);
@@ -414,8 +533,9 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
   Level &L = h->lv[li];
   const mch_desc &d = h->d;
   const int R = h->R, nc = h->nc, N = d.n_cont, P = d.periods;
-  const size_t np = L.npts, ne = (size_t)L.n * L.n;
+  const size_t np = L.npts, ne = elems(d.dim, L.n);
   const bool fp64 = d.precision == MCH_FP64;
+  const bool d3 = d.dim == 3;
   cudaStream_t st = h->st;
   h->h2d = h->d2h = 0;
   h->launches = 0;
@@ -434,13 +554,14 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
 
   // ---- constraint data
   SetupArgs sa{(int)np, L.n, P, N, R, nc, d.rve_len / L.n, d.rve_len, L.kappa, L.labels,
-               L.G, L.Sinv64, L.Sinv32, L.pstat, L.dropped, L.minv, L.nv, L.Sacc, L.bacc};
+               L.G, L.Sinv64, L.Sinv32, L.pstat, L.dropped, L.minv, L.nv, L.Sacc, L.bacc,
+               L.kap32, L.minv32};
   CK(mark(-1), "event");
-  CK(launch_setup2d(sa, st), "setup");
+  CK(d3 ? launch_setup3d(sa, st) : launch_setup2d(sa, st), "setup");
   h->launches += 2;
   CK(mark(0), "event");
 
-  const double inv_vol = 1.0 / (d.rve_len * d.rve_len);
+  const double inv_vol = 1.0 / (d3 ? d.rve_len * d.rve_len * d.rve_len : d.rve_len * d.rve_len);
   const double *g = L.G;
   const double *bvec = nullptr;
   if (li > 0) {
@@ -448,11 +569,12 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
     CK(cudaMemcpyAsync(L.gI, L.G, np * nc * R * sizeof(double), cudaMemcpyDeviceToDevice, st),
        "targets copy");
     CK(cudaMemsetAsync(L.E, 0, np * R * R * sizeof(double), st), "zero E");
-    CK(launch_child(h, L, L.gI), "child fine");
+    int nl = 0;
+    CK(launch_child(h, L, L.gI, &nl), "child fine");
     CK(launch_gram((int)np, R, L.nvf, L.phi, h->yfine, inv_vol, L.E, st), "gram I");
-    CK(launch_restrict2d((int)np, R, d.n_fine, L.rho, h->yfine, L.nvf, -1.0, L.b, L.nv, st),
-       "restrict");
-    h->launches += 3;
+    CK(launch_restrict(h, L, h->yfine, -1.0, L.b), "restrict");
+    CK(launch_bnorm((int)np, R, L.nv, L.b, L.minv, h->bnorm, st), "b norm");
+    h->launches += nl + 3;
     g = L.gI;
     bvec = L.b;
     CK(mark(1), "event");
@@ -463,7 +585,14 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
   const int max_iter = d.max_iter > 0 ? d.max_iter : 4 * L.n + 50;
   const size_t chunk = d.point_batch > 0 ? std::min(np, (size_t)d.point_batch) : np;
   int solve_launches = 0;
-  for (size_t p0 = 0; p0 < np; p0 += chunk) {
+  if (d3) {
+    CK(solve3d(h, L, g, bvec, L.x, L.iters, L.sweeps, L.ratio, L.ustat, L.lam,
+               bvec ? h->bnorm : nullptr),
+       "level 3d");
+    ++h->launches;
+    ++solve_launches;
+  }
+  for (size_t p0 = 0; p0 < np && !d3; p0 += chunk) {
     const int cn = (int)std::min(chunk, np - p0);
     const size_t u0 = p0 * R;
     const double *bb = bvec ? bvec + u0 * L.nv : nullptr;
@@ -473,14 +602,16 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
                            L.kappa + p0 * ne, L.labels + p0 * ne, L.Sinv64 + p0 * nc * nc,
                            L.Sinv64 + p0 * nc * nc, L.minv + p0 * L.nv, g + p0 * nc * R, bb,
                            L.x + u0 * L.nv, L.iters + u0, L.sweeps + u0, L.ratio + u0,
-                           L.ustat + u0, (float)d.inner_tol, max_iter, d.rtol, d.max_refine, lam};
+                           L.ustat + u0, (float)d.inner_tol, max_iter, d.rtol, d.max_refine, lam,
+                           bvec ? h->bnorm + u0 : nullptr};
       CK(launch_level2d<double>(la, st), "level fp64");
     } else {
       LevelArgs<float> la{cn, R, L.n, P, N, nc, L.nv, ilog2(L.n / P), ilog2(P),
                           L.kappa + p0 * ne, L.labels + p0 * ne, L.Sinv32 + p0 * nc * nc,
                           L.Sinv64 + p0 * nc * nc, L.minv + p0 * L.nv, g + p0 * nc * R, bb,
                           L.x + u0 * L.nv, L.iters + u0, L.sweeps + u0, L.ratio + u0,
-                          L.ustat + u0, (float)d.inner_tol, max_iter, d.rtol, d.max_refine, lam};
+                          L.ustat + u0, (float)d.inner_tol, max_iter, d.rtol, d.max_refine, lam,
+                          bvec ? h->bnorm + u0 : nullptr};
       CK(launch_level2d<float>(la, st), "level fp32");
     }
     ++h->launches;
@@ -490,7 +621,7 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
 
   // ---- effective coefficients and the cell functions on the level-1 grid
   ApplyArgs ac{(int)np, R, L.n, 1, L.nv, L.kappa, L.x, bvec, -2.0, h->yc};
-  CK(launch_apply2d(ac, st), "apply coarse");
+  CK(d3 ? launch_apply3d(ac, d.rve_len / L.n, st) : launch_apply2d(ac, st), "apply coarse");
   if (li == 0) CK(cudaMemsetAsync(L.E, 0, np * R * R * sizeof(double), st), "zero E");
   CK(launch_gram((int)np, R, L.nv, L.x, h->yc, inv_vol, L.E, st), "gram");
   h->launches += 2;
@@ -498,7 +629,7 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
     CK(cudaMemcpyAsync(L.phi, L.x, np * R * L.nv * sizeof(double), cudaMemcpyDeviceToDevice, st),
        "phi copy");
   } else {
-    CK(launch_prolong_add2d((int)np, R, d.n_fine, L.rho, L.x, L.nv, L.phi, L.nvf, st), "prolong");
+    CK(launch_prolong(h, L), "prolong");
     ++h->launches;
   }
   CK(mark(4), "event");
@@ -551,7 +682,7 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
   for (size_t u = 0; u < np * R; ++u) S.sweeps = std::max(S.sweeps, sweeps[u]);
   S.pcg_launches = solve_launches;
   for (size_t u = 0; u < np * R; ++u)
-    S.pcg_node_iters += (long long)iters[u] * (long long)(L.n - 1) * (L.n - 1);
+    S.pcg_node_iters += (long long)iters[u] * (long long)(L.n - 1) * (L.n - 1) * (d3 ? L.n - 1 : 1);
   for (size_t k = 1; k < tags.size(); ++k) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, h->ev[k - 1], h->ev[k]), "event time");
@@ -605,7 +736,8 @@ mch_status mch_cell_functions(mch_handle *h, int level, double *phi) {
   if (!L.solved) return set_err(h, MCH_ERR_ORDER, "level not solved");
   CK(restore_phi(h), "recompute cell functions");
   // library vectors are padded to nvf entries; the caller's layout is dense (n_fine+1)^2
-  const size_t row = (size_t)(h->d.n_fine + 1) * (h->d.n_fine + 1) * sizeof(double);
+  const size_t W = (size_t)h->d.n_fine + 1;
+  const size_t row = (h->d.dim == 3 ? W * W * W : W * W) * sizeof(double);
   const size_t rows = (size_t)L.npts * h->R;
   const bool dev = is_device_ptr(phi);
   if (!dev) h->d2h += (long long)(row * rows);
@@ -645,7 +777,8 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
     if (!dL_dE[l] || !dL_dkappa[l]) return set_err(h, MCH_ERR_ARG, "null gradient buffer");
   }
   cudaStream_t st = h->st;
-  const int nvf = nv_of(d.n_fine);
+  const int nvf = nvd(d.dim, d.n_fine);
+  const bool d3 = d.dim == 3;
   CK(restore_phi(h), "recompute cell functions");
   if (!h->bw_ready) {
     size_t mfine = 0, munit = 0, mnc = 0, mrr = 0, mel = 0;
@@ -655,7 +788,7 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
       munit = std::max(munit, (size_t)L.npts * R);
       mnc = std::max(mnc, (size_t)L.npts * R * nc);
       mrr = std::max(mrr, (size_t)L.npts * R * R);
-      mel = std::max(mel, (size_t)L.npts * L.n * L.n);
+      mel = std::max(mel, (size_t)L.npts * elems(d.dim, L.n));
     }
 #define BALLOC(ptr, cnt)                                               \
   do {                                                                 \
@@ -693,7 +826,8 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
   for (int l = 0; l + 1 < Lv; ++l)
     CK(cudaMemsetAsync(h->lv[l].V, 0, (size_t)h->lv[l].npts * R * nvf * sizeof(double), st),
        "zero seeds");
-  const double inv_vol = 1.0 / (d.rve_len * d.rve_len);
+  const double inv_vol = 1.0 / (d3 ? d.rve_len * d.rve_len * d.rve_len : d.rve_len * d.rve_len);
+  const double hf = d.rve_len / d.n_fine;
   const bool fp64 = d.precision == MCH_FP64;
   double worst = 0.0;
   bool breakdown = false;
@@ -705,36 +839,49 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
     if (seeds) {
       // adjoint constrained solve with right-hand side P^T V and zero targets
       if (L.rho > 1) {
-        CK(launch_restrict2d((int)np, R, d.n_fine, L.rho, L.V, nvf, 1.0, L.b, L.nv, st),
-           "restrict seeds");
+        CK(launch_restrict(h, L, L.V, 1.0, L.b), "restrict seeds");
       } else {
         CK(cudaMemcpyAsync(L.b, L.V, np * R * nvf * sizeof(double), cudaMemcpyDeviceToDevice, st),
            "copy seeds");
       }
       CK(cudaMemsetAsync(h->yc, 0, np * R * L.nv * sizeof(double), st), "zero mu");
+      CK(launch_bnorm((int)np, R, L.nv, L.b, L.minv, h->bnorm, st), "b norm");
       const int max_iter = d.max_iter > 0 ? d.max_iter : 4 * L.n + 50;
-      if (fp64) {
+      if (d3) {
+        CK(solve3d(h, L, h->gzero, L.b, h->yc, h->bw_iters, h->bw_sweeps, h->bw_ratio,
+                   h->bw_status, h->lamadj, h->bnorm),
+           "adjoint 3d");
+      } else if (fp64) {
         LevelArgs<double> la{(int)np, R, L.n, P, N, nc, L.nv, ilog2(L.n / P), ilog2(P), L.kappa,
                              L.labels, L.Sinv64, L.Sinv64, L.minv, h->gzero, L.b, h->yc,
                              h->bw_iters, h->bw_sweeps, h->bw_ratio, h->bw_status,
-                             (float)d.inner_tol, max_iter, d.rtol, d.max_refine, h->lamadj};
+                             (float)d.inner_tol, max_iter, d.rtol, d.max_refine, h->lamadj,
+                             h->bnorm};
         CK(launch_level2d<double>(la, st), "adjoint fp64");
       } else {
         LevelArgs<float> la{(int)np, R, L.n, P, N, nc, L.nv, ilog2(L.n / P), ilog2(P), L.kappa,
                             L.labels, L.Sinv32, L.Sinv64, L.minv, h->gzero, L.b, h->yc,
                             h->bw_iters, h->bw_sweeps, h->bw_ratio, h->bw_status,
-                            (float)d.inner_tol, max_iter, d.rtol, d.max_refine, h->lamadj};
+                            (float)d.inner_tol, max_iter, d.rtol, d.max_refine, h->lamadj,
+                            h->bnorm};
         CK(launch_level2d<float>(la, st), "adjoint fp32");
       }
     }
     AdjArgs aa{(int)np, R, d.n_fine, ilog2(L.rho), nvf, L.nv, nc, ilog2(d.n_fine / P), ilog2(P),
-               h->slots, inv_vol, 1.0 / ((double)L.rho * L.rho), h->Wd, L.phi,
+               h->slots, inv_vol, 1.0 / rho_pow(h, L.rho), h->Wd, L.phi,
                seeds ? h->yc : nullptr, L.lam, seeds ? h->lamadj : nullptr, L.kappa, L.labels,
                L.V, h->psi1, h->psi2, h->dk, L.par_V, L.par_w};
-    CK(launch_adj_combine2d(aa, st), "adjoint combine");
-    CK(launch_adj_grad2d(aa, st), "adjoint gradient");
-    if (li > 0) CK(launch_adj_seed2d(aa, st), "adjoint seeds");
-    CK(stage(h, dL_dkappa[li], h->dk, np * L.n * L.n * sizeof(double), false), "copy dL/dkappa");
+    if (d3) {
+      CK(launch_adj_combine3d(aa, st), "adjoint combine");
+      CK(launch_adj_grad3d(aa, hf, st), "adjoint gradient");
+      if (li > 0) CK(launch_adj_seed3d(aa, hf, st), "adjoint seeds");
+    } else {
+      CK(launch_adj_combine2d(aa, st), "adjoint combine");
+      CK(launch_adj_grad2d(aa, st), "adjoint gradient");
+      if (li > 0) CK(launch_adj_seed2d(aa, st), "adjoint seeds");
+    }
+    CK(stage(h, dL_dkappa[li], h->dk, np * elems(d.dim, L.n) * sizeof(double), false),
+       "copy dL/dkappa");
     if (seeds) {
       std::vector<double> ratio(np * R);
       std::vector<int> stat(np * R);

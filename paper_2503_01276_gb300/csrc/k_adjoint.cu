@@ -111,8 +111,10 @@ __global__ void k_adj_seed2d(AdjArgs a) {
   const uint8_t *lc = a.labels_c + (size_t)pt * ncg * ncg;
   const double *ps = a.psi1 + ((size_t)pt * R + r) * a.nvf + k;
   auto K = [&](int ex, int ey) { return kc[(ex >> lgr) + ncg * (ey >> lgr)]; };
+  const int Nm1 = (nc >> (2 * lgP)) - 1;
   auto bin = [&](int ex, int ey) {
-    return (lc[(ex >> lgr) + ncg * (ey >> lgr)] << (2 * lgP)) + ((ey >> lgmf) << lgP) + (ex >> lgmf);
+    const int l = min((int)lc[(ex >> lgr) + ncg * (ey >> lgr)], Nm1);
+    return (l << (2 * lgP)) + ((ey >> lgmf) << lgP) + (ex >> lgmf);
   };
   double u = q1_apply(K(fx - 1, fy - 1), K(fx, fy - 1), K(fx - 1, fy), K(fx, fy), ps[-Wf - 1],
                       ps[-Wf], ps[-Wf + 1], ps[-1], ps[0], ps[1], ps[Wf - 1], ps[Wf], ps[Wf + 1]);

@@ -233,10 +233,17 @@ cudaError_t launch_child_fine2d(const ChildArgs &a, cudaStream_t st) {
 
 cudaError_t launch_gram(int npts, int R, int nv, const double *X, const double *Y,
                         double alpha, double *E, cudaStream_t st) {
-  const int slices = nv >= 8192 ? 8 : (nv >= 2048 ? 4 : 1);
+  int slices = nv >= 8192 ? 8 : (nv >= 2048 ? 4 : 1);
+  if (nv > 100000) {
+    // 3D level-1 lattices: enough slices for every SM when the level has few points
+    const int want = (4 * 152 + npts - 1) / npts;
+    slices = want < 8 ? 8 : (want > nv / 4096 ? nv / 4096 : want);
+  }
   dim3 grid(npts, slices);
   switch (R) {
     case 3: k_gram2d<3><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+    case 4: k_gram2d<4><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+    case 8: k_gram2d<8><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
     case 6: k_gram2d<6><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
     case 9: k_gram2d<9><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
     case 12: k_gram2d<12><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;

@@ -1,0 +1,439 @@
+// 3D level-1-grid (fine) work of a child level, the level-grid apply for the effective
+// coefficients, and the 3D backward kernels; all FP64.
+//
+// Sec. 3.3, Eqs. (PhiXiI), (phiXiI_all): I = sum_t c_t Phi_t on the level-1 grid.
+// Eqs. (phi_avar_corrector), (phi_grad_corrector): b = -P^T A_1 I and g = G - C_1 I, with A_1
+// the level-1 stiffness of the child's medium (prolonged piecewise constantly from its
+// level-n grid); Eq. (Bs_defi): E starts from K_I = I^T A_1 I (Gram of I and A_1 I).
+// Phi = I + P Xi after the correction solve (trilinear nested prolongation P).
+//
+// Backward (see k_adjoint.cu for the 2D form and the derivation): Psi' = sum_r What_rs Phi_r
+// - P mu_s, Psi = 1/2 sum_r What_rs Phi_r - P mu_s; dL/dkappa_E = sum_{fine e in E}
+// h_f Psi_s|e^T Khat Phi_s|e; U_r = V_r + A_1 Psi'_r + rho^-3 Ct_1^T sigma_r pushed to the
+// parents.
+#include "k3d.cuh"
+#include "kernels.h"
+
+namespace mch {
+
+namespace {
+
+constexpr int F3_THREADS = 256;
+
+__device__ __forceinline__ size_t cidx(int ex, int ey, int ez, int n) {
+  return (size_t)ex + (size_t)n * (ey + (size_t)n * ez);
+}
+
+// conductivity of the fine element (ex, ey, ez) from the (nf >> lgr)-grid
+__device__ __forceinline__ double kc_of(const double *kc, int ex, int ey, int ez, int lgr,
+                                        int ncg) {
+  return kc[cidx(ex >> lgr, ey >> lgr, ez >> lgr, ncg)];
+}
+
+// y = h A(kappa) x + cb b; one thread per lattice entry (boundary and padding written as 0).
+__global__ void __launch_bounds__(F3_THREADS) k_apply3d(ApplyArgs a, double h) {
+  const int unit = blockIdx.y, pt = unit / a.R;
+  const int n = a.n, W = n + 1, lgr = __ffs(a.rho) - 1, ncg = n / a.rho;
+  const int k = blockIdx.x * F3_THREADS + threadIdx.x;
+  if (k >= a.nv) return;
+  double *y = a.y + (size_t)unit * a.nv;
+  const int kx = k % W, ky = (k / W) % W, kz = k / (W * W);
+  if (k >= W * W * W || kx == 0 || ky == 0 || kz == 0 || kx == n || ky == n || kz == n) {
+    y[k] = 0.0;
+    return;
+  }
+  const double *x = a.x + (size_t)unit * a.nv;
+  const double *kc = a.kappa + (size_t)pt * ncg * ncg * ncg;
+  double v[3][3][3], kk[2][2][2];
+#pragma unroll
+  for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx)
+        v[dz][dy][dx] = x[k + (dx - 1) + W * (dy - 1) + W * W * (dz - 1)];
+#pragma unroll
+  for (int sz = 0; sz < 2; ++sz)
+#pragma unroll
+    for (int sy = 0; sy < 2; ++sy)
+#pragma unroll
+      for (int sx = 0; sx < 2; ++sx)
+        kk[sz][sy][sx] = kc_of(kc, kx - 1 + sx, ky - 1 + sy, kz - 1 + sz, lgr, ncg);
+  double r = h * q1_apply3d<double>(v, kk);
+  if (a.b) r += a.cb * a.b[(size_t)unit * a.nv + k];
+  y[k] = r;
+}
+
+__global__ void __launch_bounds__(F3_THREADS) k_interp3d(ChildArgs a) {
+  const int unit = blockIdx.y, pt = unit / a.R, r = unit % a.R;
+  const int k = blockIdx.x * F3_THREADS + threadIdx.x;
+  if (k >= a.nvf) return;
+  double v = 0.0;
+  for (int s = 0; s < a.slots; ++s) {
+    const double w = a.par_w[pt * a.slots + s];
+    if (w != 0.0) v += w * a.par_ptr[pt * a.slots + s][(size_t)r * a.nvf + k];
+  }
+  a.phi[(size_t)unit * a.nvf + k] = v;
+}
+
+// y = h_f A_1 phi and g -= s C_1 phi: one thread per interior node column of the level-1
+// lattice, walking z with sliding windows; the constraint functionals go per (element
+// column, label) into registers, per CTA into shared memory, then into g.
+template <int NCN>
+__global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double hf) {
+  const int unit = blockIdx.y, pt = unit / a.R, r = unit % a.R;
+  const int nf = a.nf, W = nf + 1, ni = nf - 1, lgr = a.lgr, ncg = nf >> lgr;
+  const int P = 1 << a.lgP, mf = 1 << a.lgmf, nq = P * P * P;
+  __shared__ double bins[MCH_MAX_NC3];
+  for (int i = threadIdx.x; i < a.nc; i += F3_THREADS) bins[i] = 0.0;
+  __syncthreads();
+  const int t = blockIdx.x * F3_THREADS + threadIdx.x;
+  if (t < ni * ni) {
+    const int kx = 1 + t % ni, ky = 1 + t / ni;
+    const size_t W2 = (size_t)W * W;
+    const double *ph = a.phi + (size_t)unit * a.nvf;
+    double *y = a.y + (size_t)unit * a.nvf;
+    const double *kc = a.kappa_c + (size_t)pt * ncg * ncg * ncg;
+    const uint8_t *lc = a.labels_c + (size_t)pt * ncg * ncg * ncg;
+    const size_t base = kx + (size_t)W * ky;
+    double v[3][3][3], kk[2][2][2];
+    int lo[2][2], up[2][2];
+    auto load_v = [&](double (&pl)[3][3], int z) {
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) pl[dy][dx] = ph[base + W2 * z + (dx - 1) + W * (dy - 1)];
+    };
+    auto load_k = [&](double (&pl)[2][2], int (&lp)[2][2], int ez) {
+#pragma unroll
+      for (int sy = 0; sy < 2; ++sy)
+#pragma unroll
+        for (int sx = 0; sx < 2; ++sx) {
+          const size_t c = cidx((kx - 1 + sx) >> lgr, (ky - 1 + sy) >> lgr, ez >> lgr, ncg);
+          pl[sy][sx] = kc[c];
+          lp[sy][sx] = lc[c];
+        }
+    };
+    load_v(v[0], 0);
+    load_v(v[1], 1);
+    load_k(kk[0], lo, 0);
+    double acc[4][NCN];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int j = 0; j < NCN; ++j) acc[c][j] = 0.0;
+    int zb = 0;
+    auto flush = [&]() {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int ex = kx - 1 + (c & 1), ey = ky - 1 + (c >> 1);
+        const int bb = (zb * P + (ey >> a.lgmf)) * P + (ex >> a.lgmf);
+#pragma unroll
+        for (int j = 0; j < NCN; ++j) {
+          if (acc[c][j] != 0.0) atomicAdd(&bins[j * nq + bb], acc[c][j]);
+          acc[c][j] = 0.0;
+        }
+      }
+    };
+    for (int kz = 1; kz < nf; ++kz) {
+      load_v(v[2], kz + 1);
+      load_k(kk[1], up, kz);
+      const double val = v[1][1][1];
+      y[base + W2 * kz] = hf * q1_apply3d<double>(v, kk);
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int j = 0; j < NCN; ++j) acc[c][j] += (lo[c >> 1][c & 1] == j) ? val : 0.0;
+      if ((kz & (mf - 1)) == 0) {
+        flush();
+        zb = kz / mf;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int j = 0; j < NCN; ++j) acc[c][j] += (up[c >> 1][c & 1] == j) ? val : 0.0;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+          v[0][i][j] = v[1][i][j];
+          v[1][i][j] = v[2][i][j];
+        }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+          kk[0][i][j] = kk[1][i][j];
+          lo[i][j] = up[i][j];
+        }
+    }
+    flush();
+  }
+  __syncthreads();
+  double *g = a.g + (size_t)pt * a.nc * a.R + r;
+  for (int i = threadIdx.x; i < a.nc; i += F3_THREADS)
+    if (bins[i] != 0.0) atomicAdd(&g[(size_t)i * a.R], -a.s * bins[i]);
+}
+
+// out = scale P^T y on the coarse lattice (one thread per coarse lattice entry).
+__global__ void __launch_bounds__(F3_THREADS) k_restrict3d(int nf, int lgr, const double *yf,
+                                                           int nvf, double scale, double *outc,
+                                                           int nvc) {
+  const int unit = blockIdx.y;
+  const int rho = 1 << lgr, ncg = nf >> lgr, Wc = ncg + 1, Wf = nf + 1;
+  const int k = blockIdx.x * F3_THREADS + threadIdx.x;
+  if (k >= nvc) return;
+  double *o = outc + (size_t)unit * nvc;
+  const int Kx = k % Wc, Ky = (k / Wc) % Wc, Kz = k / (Wc * Wc);
+  if (k >= Wc * Wc * Wc || Kx == 0 || Ky == 0 || Kz == 0 || Kx == ncg || Ky == ncg ||
+      Kz == ncg) {
+    o[k] = 0.0;
+    return;
+  }
+  const double *y = yf + (size_t)unit * nvf;
+  const double ir = 1.0 / rho;  // exact: rho is a power of two
+  double s = 0.0;
+  for (int dz = 1 - rho; dz < rho; ++dz) {
+    const double wz = 1.0 - fabs((double)dz) * ir;
+    const int fz = Kz * rho + dz;
+    double sy = 0.0;
+    for (int dy = 1 - rho; dy < rho; ++dy) {
+      const double wy = 1.0 - fabs((double)dy) * ir;
+      const size_t row = (size_t)Wf * ((Kz * rho + dz) * (size_t)Wf + Ky * rho + dy);
+      double sx = 0.0;
+      for (int dx = 1 - rho; dx < rho; ++dx)
+        sx += (1.0 - fabs((double)dx) * ir) * y[row + Kx * rho + dx];
+      sy += wy * sx;
+    }
+    s += wz * sy;
+    (void)fz;
+  }
+  o[k] = scale * s;
+}
+
+// phi += P x_c (one thread per fine lattice node).
+__global__ void __launch_bounds__(F3_THREADS) k_prolong_add3d(int nf, int lgr, const double *xc,
+                                                              int nvc, double *phif, int nvf) {
+  const int unit = blockIdx.y;
+  const int rho = 1 << lgr, ncg = nf >> lgr, Wc = ncg + 1, Wf = nf + 1;
+  const int k = blockIdx.x * F3_THREADS + threadIdx.x;
+  if (k >= Wf * Wf * Wf) return;
+  const int fx = k % Wf, fy = (k / Wf) % Wf, fz = k / (Wf * Wf);
+  const int bx = min(fx >> lgr, ncg - 1), by = min(fy >> lgr, ncg - 1), bz = min(fz >> lgr, ncg - 1);
+  const double ir = 1.0 / rho;
+  const double tx = (fx - (bx << lgr)) * ir, ty = (fy - (by << lgr)) * ir,
+               tz = (fz - (bz << lgr)) * ir;
+  const double *x = xc + (size_t)unit * nvc + bx + (size_t)Wc * (by + (size_t)Wc * bz);
+  const size_t sy = Wc, sz = (size_t)Wc * Wc;
+  const double c00 = (1 - tx) * x[0] + tx * x[1];
+  const double c10 = (1 - tx) * x[sy] + tx * x[sy + 1];
+  const double c01 = (1 - tx) * x[sz] + tx * x[sz + 1];
+  const double c11 = (1 - tx) * x[sz + sy] + tx * x[sz + sy + 1];
+  const double c0 = (1 - ty) * c00 + ty * c10, c1 = (1 - ty) * c01 + ty * c11;
+  phif[(size_t)unit * nvf + k] += (1 - tz) * c0 + tz * c1;
+  (void)rho;
+}
+
+// ---- backward
+
+template <int R>
+__global__ void __launch_bounds__(F3_THREADS) k_adj_combine3d(AdjArgs a) {
+  const int pt = blockIdx.y;
+  const int nf = a.nf, Wf = nf + 1, lgr = a.lgr, ncg = nf >> lgr, Wc = ncg + 1;
+  const int k = blockIdx.x * F3_THREADS + threadIdx.x;
+  if (k >= Wf * Wf * Wf) return;
+  const int fx = k % Wf, fy = (k / Wf) % Wf, fz = k / (Wf * Wf);
+  double wh[R * R];
+  const double *Wp = a.W + (size_t)pt * R * R;
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int s = 0; s < R; ++s) wh[r * R + s] = (Wp[r * R + s] + Wp[s * R + r]) * a.inv_vol;
+  double phi[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) phi[r] = a.phi[((size_t)pt * R + r) * a.nvf + k];
+  const int bx = min(fx >> lgr, ncg - 1), by = min(fy >> lgr, ncg - 1), bz = min(fz >> lgr, ncg - 1);
+  const double ir = 1.0 / (1 << lgr);
+  const double tx = (fx - (bx << lgr)) * ir, ty = (fy - (by << lgr)) * ir,
+               tz = (fz - (bz << lgr)) * ir;
+  const size_t c0 = bx + (size_t)Wc * (by + (size_t)Wc * bz), sy = Wc, sz = (size_t)Wc * Wc;
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    double x = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) x += wh[r * R + s] * phi[r];
+    double pm = 0.0;
+    if (a.mu) {
+      const double *m = a.mu + ((size_t)pt * R + s) * a.nvc + c0;
+      const double e00 = (1 - tx) * m[0] + tx * m[1], e10 = (1 - tx) * m[sy] + tx * m[sy + 1];
+      const double e01 = (1 - tx) * m[sz] + tx * m[sz + 1];
+      const double e11 = (1 - tx) * m[sz + sy] + tx * m[sz + sy + 1];
+      pm = (1 - tz) * ((1 - ty) * e00 + ty * e10) + tz * ((1 - ty) * e01 + ty * e11);
+    }
+    const size_t o = ((size_t)pt * R + s) * a.nvf + k;
+    a.psi1[o] = x - pm;
+    a.psi2[o] = 0.5 * x - pm;
+  }
+}
+
+// dL/dkappa per coarse element: one thread per (point, coarse element).
+template <int R>
+__global__ void __launch_bounds__(F3_THREADS) k_adj_grad3d(AdjArgs a, double hf) {
+  const int pt = blockIdx.y;
+  const int nf = a.nf, Wf = nf + 1, lgr = a.lgr, rho = 1 << lgr, ncg = nf >> lgr;
+  const int E = blockIdx.x * F3_THREADS + threadIdx.x;
+  if (E >= ncg * ncg * ncg) return;
+  const int Ex = E % ncg, Ey = (E / ncg) % ncg, Ez = E / (ncg * ncg);
+  const size_t sy = Wf, sz = (size_t)Wf * Wf;
+  double g = 0.0;
+  for (int kz = 0; kz < rho; ++kz)
+    for (int jy = 0; jy < rho; ++jy)
+      for (int ix = 0; ix < rho; ++ix) {
+        const size_t k0 = (Ex * rho + ix) + sy * (Ey * rho + jy) + sz * (Ez * rho + kz);
+        const size_t off[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
+#pragma unroll
+        for (int s = 0; s < R; ++s) {
+          const size_t o = ((size_t)pt * R + s) * a.nvf + k0;
+          double p[8], q[8];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            p[c] = a.phi[o + off[c]];
+            q[c] = a.psi2[o + off[c]];
+          }
+          // Khat p at corner c: 1/3 p_c - 1/12 (sum of the 3 face-diagonal corners c^3, c^5,
+          // c^6 and the opposite corner c^7); axis neighbours do not couple
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const double kp = p[c] * (1.0 / 3.0) -
+                              (p[c ^ 3] + p[c ^ 5] + p[c ^ 6] + p[c ^ 7]) * (1.0 / 12.0);
+            g += q[c] * kp;
+          }
+        }
+      }
+  a.dkappa[(size_t)pt * ncg * ncg * ncg + E] = g * hf;
+}
+
+template <int NCN>
+__global__ void __launch_bounds__(F3_THREADS) k_adj_seed3d(AdjArgs a, double hf) {
+  const int unit = blockIdx.y;
+  const int R = a.R, pt = unit / R, r = unit % R;
+  const int nf = a.nf, Wf = nf + 1, lgr = a.lgr, ncg = nf >> lgr, nc = a.nc;
+  const int lgmf = a.lgmf, lgP = a.lgP, P = 1 << lgP;
+  __shared__ double sig[MCH_MAX_NC3];
+  for (int b = threadIdx.x; b < nc; b += F3_THREADS) {
+    double sgm = 0.0;
+    const double *Wp = a.W + (size_t)pt * R * R;
+    for (int s = 0; s < R; ++s)
+      sgm += (Wp[r * R + s] + Wp[s * R + r]) * a.inv_vol * a.lam[((size_t)pt * R + s) * nc + b];
+    if (a.lamadj) sgm -= a.lamadj[((size_t)pt * R + r) * nc + b];
+    sig[b] = sgm * a.inv_rho2;
+  }
+  __syncthreads();
+  const int k = blockIdx.x * F3_THREADS + threadIdx.x;
+  if (k >= Wf * Wf * Wf) return;
+  const int fx = k % Wf, fy = (k / Wf) % Wf, fz = k / (Wf * Wf);
+  if (fx == 0 || fy == 0 || fz == 0 || fx == nf || fy == nf || fz == nf) return;
+  const double *kc = a.kappa_c + (size_t)pt * ncg * ncg * ncg;
+  const uint8_t *lc = a.labels_c + (size_t)pt * ncg * ncg * ncg;
+  const double *ps = a.psi1 + ((size_t)pt * R + r) * a.nvf;
+  double v[3][3][3], kk[2][2][2];
+  double u = 0.0;
+  const size_t W2 = (size_t)Wf * Wf;
+#pragma unroll
+  for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+    for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 3; ++dx) v[dz][dy][dx] = ps[k + (dx - 1) + Wf * (dy - 1) + W2 * (dz - 1)];
+#pragma unroll
+  for (int sz = 0; sz < 2; ++sz)
+#pragma unroll
+    for (int sy = 0; sy < 2; ++sy)
+#pragma unroll
+      for (int sx = 0; sx < 2; ++sx) {
+        const int ex = fx - 1 + sx, ey = fy - 1 + sy, ez = fz - 1 + sz;
+        const size_t c = cidx(ex >> lgr, ey >> lgr, ez >> lgr, ncg);
+        kk[sz][sy][sx] = kc[c];
+        const int l = min((int)lc[c], (nc >> (3 * lgP)) - 1);
+        const int bin = (l << (3 * lgP)) + (((ez >> lgmf) * P + (ey >> lgmf)) << lgP) + (ex >> lgmf);
+        u += sig[bin];
+      }
+  u += hf * q1_apply3d<double>(v, kk);
+  if (a.V) u += a.V[((size_t)pt * R + r) * a.nvf + k];
+  for (int t = 0; t < a.slots; ++t) {
+    const double w = a.par_w[pt * a.slots + t];
+    if (w != 0.0) atomicAdd(&a.par_V[pt * a.slots + t][(size_t)r * a.nvf + k], w * u);
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_apply3d(const ApplyArgs &a, double h, cudaStream_t st) {
+  dim3 grid((a.nv + F3_THREADS - 1) / F3_THREADS, a.npts * a.R);
+  k_apply3d<<<grid, F3_THREADS, 0, st>>>(a, h);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_interp3d(const ChildArgs &a, cudaStream_t st) {
+  dim3 grid((a.nvf + F3_THREADS - 1) / F3_THREADS, a.npts * a.R);
+  k_interp3d<<<grid, F3_THREADS, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fine_apply3d(const ChildArgs &a, double hf, cudaStream_t st) {
+  if (a.nc > MCH_MAX_NC3) return cudaErrorInvalidValue;
+  const int ni = a.nf - 1;
+  dim3 grid((ni * ni + F3_THREADS - 1) / F3_THREADS, a.npts * a.R);
+  if (a.N <= 2) k_fine_apply3d<2><<<grid, F3_THREADS, 0, st>>>(a, hf);
+  else k_fine_apply3d<4><<<grid, F3_THREADS, 0, st>>>(a, hf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict3d(int npts, int R, int nf, int rho, const double *yf, int nvf,
+                              double scale, double *outc, int nvc, cudaStream_t st) {
+  dim3 grid((nvc + F3_THREADS - 1) / F3_THREADS, npts * R);
+  k_restrict3d<<<grid, F3_THREADS, 0, st>>>(nf, __builtin_ctz(rho), yf, nvf, scale, outc, nvc);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong_add3d(int npts, int R, int nf, int rho, const double *xc, int nvc,
+                                 double *phif, int nvf, cudaStream_t st) {
+  const int Wf = nf + 1;
+  dim3 grid((Wf * Wf * Wf + F3_THREADS - 1) / F3_THREADS, npts * R);
+  k_prolong_add3d<<<grid, F3_THREADS, 0, st>>>(nf, __builtin_ctz(rho), xc, nvc, phif, nvf);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_combine3d(const AdjArgs &a, cudaStream_t st) {
+  const int Wf = a.nf + 1;
+  dim3 grid((Wf * Wf * Wf + F3_THREADS - 1) / F3_THREADS, a.npts);
+  switch (a.R) {
+    case 4: k_adj_combine3d<4><<<grid, F3_THREADS, 0, st>>>(a); break;
+    case 8: k_adj_combine3d<8><<<grid, F3_THREADS, 0, st>>>(a); break;
+    case 12: k_adj_combine3d<12><<<grid, F3_THREADS, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_grad3d(const AdjArgs &a, double hf, cudaStream_t st) {
+  const int ncg = a.nf >> a.lgr;
+  dim3 grid((ncg * ncg * ncg + F3_THREADS - 1) / F3_THREADS, a.npts);
+  switch (a.R) {
+    case 4: k_adj_grad3d<4><<<grid, F3_THREADS, 0, st>>>(a, hf); break;
+    case 8: k_adj_grad3d<8><<<grid, F3_THREADS, 0, st>>>(a, hf); break;
+    case 12: k_adj_grad3d<12><<<grid, F3_THREADS, 0, st>>>(a, hf); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adj_seed3d(const AdjArgs &a, double hf, cudaStream_t st) {
+  if (a.nc > MCH_MAX_NC3) return cudaErrorInvalidValue;
+  const int Wf = a.nf + 1;
+  dim3 grid((Wf * Wf * Wf + F3_THREADS - 1) / F3_THREADS, a.npts * a.R);
+  k_adj_seed3d<2><<<grid, F3_THREADS, 0, st>>>(a, hf);
+  return cudaGetLastError();
+}
+
+}  // namespace mch

@@ -39,4 +39,32 @@ cudaError_t launch_apply2d(const ApplyArgs &a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+namespace {
+
+__global__ void __launch_bounds__(256) k_bnorm(int R, int nv, const double *b, const double *minv,
+                                               double *out) {
+  const int unit = blockIdx.x, pt = unit / R;
+  const double *bb = b + (size_t)unit * nv;
+  const double *mm = minv + (size_t)pt * nv;
+  double s = 0.0;
+  for (int k = threadIdx.x; k < nv; k += 256) s += bb[k] * bb[k] * mm[k];
+  s = warp_sum(s);
+  __shared__ double red[8];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t += red[w];
+    out[unit] = t;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_bnorm(int npts, int R, int nv, const double *b, const double *minv,
+                         double *out, cudaStream_t st) {
+  k_bnorm<<<npts * R, 256, 0, st>>>(R, nv, b, minv, out);
+  return cudaGetLastError();
+}
+
 }  // namespace mch

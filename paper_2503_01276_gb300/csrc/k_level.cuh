@@ -14,7 +14,11 @@
 // the correction data of Eqs. phi_avar_corrector / phi_grad_corrector). Loop:
 //   FP64 refinement step: x += delta; x += M^-1 Ct^T S^-1 (g - Ct x)  (constraints exact);
 //     r = b - A x; r <- r - Ct^T S^-1 Ct M^-1 r; rho64 = r'M^-1 r; stop when
-//     sqrt(rho64 / rho64_first) < rtol, else hand r to the next sweep as its residual.
+//     sqrt(rho64 / rho64_ref) < rtol, else hand r to the next sweep as its residual.
+//     rho64_ref = max(rho64 of the first step, b'M^-1 b): for a correction problem (n > 1)
+//     the right-hand side b = -P^T A_1 I carries the scale of the cell function I + P Xi,
+//     so the test bounds the error of the cell function, not of the (possibly tiny)
+//     correction.
 //   inner sweep (projected PCG, inner precision, from delta = 0):
 //     q = A p
 //     one reduction of  p.q, z.q, q.M^-1 q, r.z, Ct z, Ct M^-1 q   (z = M^-1 r)
@@ -165,7 +169,9 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
     const int ey = r_lo - 1 + t / NEL, ex = t % NEL;
     const bool in = ey < n;
     ks[t] = in ? T(kap[ex + n * ey]) : T(0);
-    ls[t] = in ? lab[ex + n * ey] : uint8_t(0);
+    // labels >= N (invalid input, reported by the setup) are clamped so that no row index
+    // leaves the multiplier table
+    ls[t] = in ? (uint8_t)min((int)lab[ex + n * ey], a.N - 1) : uint8_t(0);
   }
   {
     const T *Si = a.Sinv + (size_t)pt * nc * nc;
@@ -402,7 +408,7 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
     {
       double sum = 0.0;
       for (int rk = 0; rk < CL; ++rk) sum += C::remote(red64, rk)[2 * nc];
-      if (step == 0) rho64_first = sum;
+      if (step == 0) rho64_first = a.bnorm ? fmax(sum, a.bnorm[unit]) : sum;
       ratio = rho64_first > 0.0 ? sqrt(sum / rho64_first) : 0.0;
       if (!(ratio >= a.rtol)) done = true;
       if (!(ratio == ratio)) breakdown = true;

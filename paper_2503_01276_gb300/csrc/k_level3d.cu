@@ -1,0 +1,692 @@
+// Persistent level solve for the 3D constrained cell problems.
+//
+// Same method as the 2D level kernel (Sec. 3, Eq. phi_abstract: minimise 1/2 x'A x - b'x
+// subject to Ct x = g, FP64 refinement steps around projected Jacobi-PCG sweeps in the inner
+// precision T), but the 3D RVEs are too large to keep on chip (a 64^3 RVE has 250k unknowns
+// per cell function), so the vectors stream through L2 and HBM. One cooperative launch
+// covers the level: the interior node columns (kx, ky) of all (point, function) units are
+// split into contiguous ranges, one per CTA; a thread walks a column along z with sliding
+// windows of the 3x3x3 neighbourhood, of the 8 adjacent elements' kappa and of their labels.
+//
+// Per-unit reductions (dot products and the constraint functionals, which a column adds
+// for each adjacent element row from its own nodes) are summed per CTA in shared memory and
+// then atomically in FP64 into per-unit accumulators. Accumulators rotate over three buffers
+// (written in a phase, read in the next, cleared in the one before), so every phase ends
+// with exactly one grid barrier. After a barrier every CTA recomputes the scalars and the
+// small constraint solves of its own units from the same sums in the same order, so all CTAs
+// take the same decisions without further communication; loop exits use counters that the
+// units' leader CTAs increment.
+//
+// Refinement step (FP64): x += delta; x += M^-1 Ct^T S^-1 (g - Ct x); r = b - A x;
+//   r <- r - Ct^T S^-1 Ct M^-1 r; rho64 = r'M^-1 r; stop at sqrt(rho64 / rho64_ref) < rtol
+//   with rho64_ref = max(rho64 of the first step, b'M^-1 b) (the scale of the cell function
+//   for a correction problem).
+// Inner iteration (T): q = A p; sums p.q, z.q, q.M^-1 q, r.z, Ct z, Ct M^-1 q;
+//   alpha = rho / p.q; c = Ct z - alpha Ct M^-1 q; lambda = S^-1 c;
+//   delta += alpha p; r <- r - alpha q - Ct^T lambda; rho' = r.z - 2 alpha z.q
+//   + alpha^2 q.M^-1 q - lambda.c; p = M^-1 r + (rho' / rho) p.
+// Every loop is bounded by max_refine and max_iter.
+#include <cooperative_groups.h>
+
+#include "k3d.cuh"
+#include "kernels.h"
+
+namespace mch {
+
+namespace cg = cooperative_groups;
+
+namespace {
+
+constexpr int L3_THREADS = 256;
+constexpr int NACC_S = 8;  // scalar sums per unit: pq, zq, qMq, rz, rho64
+
+struct L3Smem {
+  int kmax, nc;
+  double *sums;   // [kmax][8]
+  double *bins;   // [kmax][2 nc]
+  double *vec;    // [kmax][nc] multipliers of the current phase
+  double *rho, *rho_first, *rho64_first, *ratio, *alpha, *beta;  // [kmax]
+  int *flags, *iters, *sweeps;                                   // [kmax]
+};
+
+// flags bits
+constexpr int F_DONE = 1;    // unit finished (converged, capped or broken down)
+constexpr int F_INNER = 2;   // unit active in the current inner sweep
+constexpr int F_BREAK = 4;   // breakdown
+
+template <typename V>
+__device__ __forceinline__ void load_plane9(V (&v)[3][3], const V *p, size_t node, int W) {
+#pragma unroll
+  for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+    for (int dx = 0; dx < 3; ++dx) v[dy][dx] = p[node + (dx - 1) + (size_t)W * (dy - 1)];
+}
+
+template <typename V>
+__device__ __forceinline__ void load_kplane(V (&k)[2][2], const V *kap, int kx, int ky, int ez,
+                                            int n) {
+#pragma unroll
+  for (int sy = 0; sy < 2; ++sy)
+#pragma unroll
+    for (int sx = 0; sx < 2; ++sx)
+      k[sy][sx] = kap[(kx - 1 + sx) + (size_t)n * ((ky - 1 + sy) + (size_t)n * ez)];
+}
+
+// labels >= N (invalid input, reported by the setup) are clamped so that no row index leaves
+// the multiplier tables
+__device__ __forceinline__ void load_lplane(int (&l)[2][2], const uint8_t *lab, int kx, int ky,
+                                            int ez, int n, int nm1) {
+#pragma unroll
+  for (int sy = 0; sy < 2; ++sy)
+#pragma unroll
+    for (int sx = 0; sx < 2; ++sx)
+      l[sy][sx] = min((int)lab[(kx - 1 + sx) + (size_t)n * ((ky - 1 + sy) + (size_t)n * ez)], nm1);
+}
+
+// Per-column accumulation of node values into the constraint rows of the adjacent elements
+// (node-based form of Ct v): the four element columns (sx, sy) around the node column keep
+// per-label partial sums for the current z-block and flush them to shared memory.
+template <typename V, int NCN>
+struct ColBins {
+  V acc[4][NCN];
+  int zb;
+  __device__ __forceinline__ void reset() {
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int j = 0; j < NCN; ++j) acc[c][j] = V(0);
+  }
+  __device__ __forceinline__ void add(const int (&l)[2][2], V v) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int j = 0; j < NCN; ++j) acc[c][j] += (l[c >> 1][c & 1] == j) ? v : V(0);
+  }
+  __device__ __forceinline__ void flush(double *bins, int kx, int ky, int m, int P, int nq) {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int ex = kx - 1 + (c & 1), ey = ky - 1 + (c >> 1);
+      const int base = (zb * P + ey / m) * P + ex / m;
+#pragma unroll
+      for (int j = 0; j < NCN; ++j)
+        if (acc[c][j] != V(0)) atomicAdd(&bins[j * nq + base], (double)acc[c][j]);
+    }
+    reset();
+  }
+};
+
+// Ct^T vec at a node from the labels of its 8 adjacent elements (lower plane ez = kz-1,
+// upper plane ez = kz).
+__device__ __forceinline__ double ctt_node(const double *vec, const int (&lo)[2][2],
+                                           const int (&up)[2][2], int kx, int ky, int kz, int m,
+                                           int P, int nq) {
+  double s = 0.0;
+  const int zl = (kz - 1) / m, zu = kz / m;
+#pragma unroll
+  for (int sy = 0; sy < 2; ++sy)
+#pragma unroll
+    for (int sx = 0; sx < 2; ++sx) {
+      const int bxy = ((ky - 1 + sy) / m) * P + (kx - 1 + sx) / m;
+      s += vec[lo[sy][sx] * nq + zl * P * P + bxy] + vec[up[sy][sx] * nq + zu * P * P + bxy];
+    }
+  return s;
+}
+
+template <typename T>
+struct Col {
+  int u, slot, pt, kx, ky;
+};
+
+template <typename T, int NCN>
+__global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
+  cg::grid_group grid = cg::this_grid();
+  const int n = a.n, W = n + 1, ni = n - 1, R = a.R, nc = a.nc, P = a.P, m = a.m;
+  const int nq = P * P * P;
+  const long long cpu = (long long)ni * ni;
+  const long long units = (long long)a.npts * R;
+  const long long total = units * cpu;
+  const long long c0 = (long long)blockIdx.x * a.cols_per_cta;
+  const long long c1 = min(total, c0 + a.cols_per_cta);
+  const int u0 = (int)(c0 / cpu);
+  const int K = c1 > c0 ? (int)((c1 - 1) / cpu) - u0 + 1 : 0;
+  const int tid = threadIdx.x;
+  const int NACC = NACC_S + 2 * nc;
+  const size_t bufsz = (size_t)units * NACC;
+  const size_t W2 = (size_t)W * W;
+
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  L3Smem S;
+  {
+    double *d = reinterpret_cast<double *>(smem_raw);
+    const int km = a.kmax;
+    S.kmax = km;
+    S.nc = nc;
+    S.sums = d;
+    d += km * 8;
+    S.bins = d;
+    d += km * 2 * nc;
+    S.vec = d;
+    d += km * nc;
+    S.rho = d;
+    d += km;
+    S.rho_first = d;
+    d += km;
+    S.rho64_first = d;
+    d += km;
+    S.ratio = d;
+    d += km;
+    S.alpha = d;
+    d += km;
+    S.beta = d;
+    d += km;
+    int *ip = reinterpret_cast<int *>(d);
+    S.flags = ip;
+    ip += km;
+    S.iters = ip;
+    ip += km;
+    S.sweeps = ip;
+  }
+  for (int s = tid; s < K; s += L3_THREADS) {
+    S.flags[s] = 0;
+    S.iters[s] = 0;
+    S.sweeps[s] = 0;
+    S.ratio[s] = 0.0;
+  }
+  int ph = 0;
+  auto wbuf = [&]() { return a.acc + (size_t)(ph % 3) * bufsz; };
+  auto rbuf = [&]() { return a.acc + (size_t)((ph + 2) % 3) * bufsz; };
+  auto leader = [&](int u) { return (long long)blockIdx.x == ((long long)u * cpu) / a.cols_per_cta; };
+  // clears the buffer of the next phase (units whose leader this CTA is) and its counter
+  auto clear_next = [&]() {
+    double *z = a.acc + (size_t)((ph + 1) % 3) * bufsz;
+    for (int s = 0; s < K; ++s) {
+      const int u = u0 + s;
+      if (!leader(u)) continue;
+      for (int i = tid; i < NACC; i += L3_THREADS) z[(size_t)u * NACC + i] = 0.0;
+    }
+    if (blockIdx.x == 0 && tid == 0) a.cnt[(ph + 1) % 3] = 0;
+  };
+  auto zero_local = [&]() {
+    for (int i = tid; i < K * 8; i += L3_THREADS) S.sums[i] = 0.0;
+    for (int i = tid; i < K * 2 * nc; i += L3_THREADS) S.bins[i] = 0.0;
+  };
+  // adds the CTA's shared sums of slot s to the unit's accumulator (nonzero entries only)
+  auto push_local = [&](int nbins) {
+    double *w = wbuf();
+    for (int s = 0; s < K; ++s) {
+      const size_t ub = (size_t)(u0 + s) * NACC;
+      for (int i = tid; i < NACC_S + nbins; i += L3_THREADS) {
+        const double v = i < NACC_S ? S.sums[s * 8 + i] : S.bins[s * 2 * nc + (i - NACC_S)];
+        if (v != 0.0) atomicAdd(&w[ub + i], v);
+      }
+    }
+  };
+  auto sync = [&]() {
+    grid.sync();
+    ++ph;
+  };
+  auto col_of = [&](long long c, Col<T> &cl) {
+    cl.u = (int)(c / cpu);
+    cl.slot = cl.u - u0;
+    const int t = (int)(c % cpu);
+    cl.kx = 1 + t % ni;
+    cl.ky = 1 + t / ni;
+    cl.pt = cl.u / R;
+  };
+  // S^-1 v per slot (FP64 rows read column-wise: S^-1 is symmetric); v from `src`
+  // ([slot][nc] with stride), result in S.vec.
+  auto small_solve64 = [&](int s, const double *src, double sign, const double *gsub) {
+    const int pt = (u0 + s) / R;
+    const double *Si = a.Sinv64 + (size_t)pt * nc * nc;
+    for (int i = tid; i < nc; i += L3_THREADS) {
+      double acc = 0.0;
+      for (int j = 0; j < nc; ++j) {
+        const double cj = gsub ? gsub[(size_t)j * R] - src[j] : sign * src[j];
+        acc += Si[(size_t)j * nc + i] * cj;
+      }
+      S.vec[s * nc + i] = acc;
+    }
+  };
+
+  const int max_refine = a.max_refine;
+  bool finished = false;
+  for (int sweep = 0; sweep <= max_refine && !finished; ++sweep) {
+    // ---- F1: x += delta, delta = 0; Ct x
+    clear_next();
+    zero_local();
+    __syncthreads();
+    for (long long c = c0 + tid; c < c1; c += L3_THREADS) {
+      Col<T> cl;
+      col_of(c, cl);
+      if (S.flags[cl.slot] & F_DONE) continue;
+      const size_t ub = (size_t)cl.u * a.nv + cl.kx + (size_t)W * cl.ky;
+      const uint8_t *lab = a.labels + (size_t)cl.pt * n * n * n;
+      ColBins<double, NCN> cb;
+      cb.reset();
+      cb.zb = 0;
+      int lo[2][2], up[2][2];
+      load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
+      double *sb = S.bins + cl.slot * 2 * nc;
+      for (int kz = 1; kz < n; ++kz) {
+        load_lplane(up, lab, cl.kx, cl.ky, kz, n, a.N - 1);
+        const size_t o = ub + W2 * kz;
+        double xv = a.x[o];
+        if (sweep > 0) {
+          xv += (double)a.d[o];
+          a.x[o] = xv;
+          a.d[o] = T(0);
+        }
+        cb.add(lo, xv);
+        if (kz % m == 0) {
+          cb.flush(sb, cl.kx, cl.ky, m, P, nq);
+          cb.zb = kz / m;
+        }
+        cb.add(up, xv);
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) lo[i][j] = up[i][j];
+      }
+      cb.flush(sb, cl.kx, cl.ky, m, P, nq);
+    }
+    __syncthreads();
+    push_local(nc);
+    sync();
+
+    // ---- F2: mu = S^-1 (g - Ct x); x += M^-1 Ct^T mu
+    clear_next();
+    {
+      const double *rb = rbuf();
+      for (int s = 0; s < K; ++s) {
+        if (S.flags[s] & F_DONE) continue;
+        const int u = u0 + s, pt = u / R, rf = u % R;
+        small_solve64(s, rb + (size_t)u * NACC + NACC_S, 1.0, a.g + (size_t)pt * nc * R + rf);
+      }
+    }
+    __syncthreads();
+    for (long long c = c0 + tid; c < c1; c += L3_THREADS) {
+      Col<T> cl;
+      col_of(c, cl);
+      if (S.flags[cl.slot] & F_DONE) continue;
+      const size_t ub = (size_t)cl.u * a.nv + cl.kx + (size_t)W * cl.ky;
+      const size_t mb = (size_t)cl.pt * a.nv + cl.kx + (size_t)W * cl.ky;
+      const uint8_t *lab = a.labels + (size_t)cl.pt * n * n * n;
+      const double *vec = S.vec + cl.slot * nc;
+      int lo[2][2], up[2][2];
+      load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
+      for (int kz = 1; kz < n; ++kz) {
+        load_lplane(up, lab, cl.kx, cl.ky, kz, n, a.N - 1);
+        const size_t o = ub + W2 * kz;
+        a.x[o] += a.minv64[mb + W2 * kz] * ctt_node(vec, lo, up, cl.kx, cl.ky, kz, m, P, nq);
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) lo[i][j] = up[i][j];
+      }
+    }
+    sync();
+
+    // ---- F3: r = b - A x (FP64); Ct M^-1 r
+    clear_next();
+    zero_local();
+    __syncthreads();
+    for (long long c = c0 + tid; c < c1; c += L3_THREADS) {
+      Col<T> cl;
+      col_of(c, cl);
+      if (S.flags[cl.slot] & F_DONE) continue;
+      const size_t ub = (size_t)cl.u * a.nv + cl.kx + (size_t)W * cl.ky;
+      const size_t mb = (size_t)cl.pt * a.nv + cl.kx + (size_t)W * cl.ky;
+      const uint8_t *lab = a.labels + (size_t)cl.pt * n * n * n;
+      const double *kap = a.kappa + (size_t)cl.pt * n * n * n;
+      const double *bb = a.b ? a.b + (size_t)cl.u * a.nv : nullptr;
+      double v[3][3][3], k[2][2][2];
+      load_plane9(v[0], a.x, ub, W);
+      load_plane9(v[1], a.x, ub + W2, W);
+      load_kplane(k[0], kap, cl.kx, cl.ky, 0, n);
+      int lo[2][2], up[2][2];
+      load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
+      ColBins<double, NCN> cb;
+      cb.reset();
+      cb.zb = 0;
+      double *sb = S.bins + cl.slot * 2 * nc;
+      for (int kz = 1; kz < n; ++kz) {
+        load_plane9(v[2], a.x, ub + W2 * (kz + 1), W);
+        load_kplane(k[1], kap, cl.kx, cl.ky, kz, n);
+        load_lplane(up, lab, cl.kx, cl.ky, kz, n, a.N - 1);
+        const size_t o = ub + W2 * kz;
+        double r = -a.h * q1_apply3d<double>(v, k);
+        if (bb) r += bb[o - (size_t)cl.u * a.nv];
+        a.r64[o] = r;
+        const double mr = a.minv64[mb + W2 * kz] * r;
+        cb.add(lo, mr);
+        if (kz % m == 0) {
+          cb.flush(sb, cl.kx, cl.ky, m, P, nq);
+          cb.zb = kz / m;
+        }
+        cb.add(up, mr);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+          for (int j = 0; j < 3; ++j) {
+            v[0][i][j] = v[1][i][j];
+            v[1][i][j] = v[2][i][j];
+          }
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            k[0][i][j] = k[1][i][j];
+            lo[i][j] = up[i][j];
+          }
+      }
+      cb.flush(sb, cl.kx, cl.ky, m, P, nq);
+    }
+    __syncthreads();
+    push_local(nc);
+    sync();
+
+    // ---- F4: lambda = S^-1 Ct M^-1 r; r -= Ct^T lambda; rho64; inner vectors
+    clear_next();
+    zero_local();
+    {
+      const double *rb = rbuf();
+      for (int s = 0; s < K; ++s) {
+        if (S.flags[s] & F_DONE) continue;
+        const int u = u0 + s;
+        small_solve64(s, rb + (size_t)u * NACC + NACC_S, 1.0, nullptr);
+      }
+    }
+    __syncthreads();
+    for (int s = 0; s < K; ++s) {
+      const int u = u0 + s;
+      if ((S.flags[s] & F_DONE) || !a.lam || !leader(u)) continue;
+      for (int i = tid; i < nc; i += L3_THREADS) a.lam[(size_t)u * nc + i] = S.vec[s * nc + i];
+    }
+    for (long long c = c0 + tid; c < c1; c += L3_THREADS) {
+      Col<T> cl;
+      col_of(c, cl);
+      if (S.flags[cl.slot] & F_DONE) continue;
+      const size_t ub = (size_t)cl.u * a.nv + cl.kx + (size_t)W * cl.ky;
+      const size_t mb = (size_t)cl.pt * a.nv + cl.kx + (size_t)W * cl.ky;
+      const uint8_t *lab = a.labels + (size_t)cl.pt * n * n * n;
+      const double *vec = S.vec + cl.slot * nc;
+      int lo[2][2], up[2][2];
+      load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
+      double rho = 0.0;
+      for (int kz = 1; kz < n; ++kz) {
+        load_lplane(up, lab, cl.kx, cl.ky, kz, n, a.N - 1);
+        const size_t o = ub + W2 * kz;
+        const double r = a.r64[o] - ctt_node(vec, lo, up, cl.kx, cl.ky, kz, m, P, nq);
+        const double mi = a.minv64[mb + W2 * kz];
+        rho += r * mi * r;
+        const T rt = (T)r;
+        a.r[o] = rt;
+        a.p[o] = a.minvT[mb + W2 * kz] * rt;
+#pragma unroll
+        for (int i = 0; i < 2; ++i)
+#pragma unroll
+          for (int j = 0; j < 2; ++j) lo[i][j] = up[i][j];
+      }
+      atomicAdd(&S.sums[cl.slot * 8 + 4], rho);
+    }
+    __syncthreads();
+    push_local(0);
+    sync();
+
+    // ---- F5 (no barrier of its own): refinement decisions; then the inner sweep
+    {
+      const double *rb = rbuf();
+      if (tid == 0) {
+        for (int s = 0; s < K; ++s) {
+          if (S.flags[s] & F_DONE) continue;
+          const int u = u0 + s;
+          const double r64 = rb[(size_t)u * NACC + 4];
+          if (sweep == 0) S.rho64_first[s] = a.bnorm ? fmax(r64, a.bnorm[u]) : r64;
+          const double f = S.rho64_first[s];
+          const double ratio = f > 0.0 ? sqrt(r64 / f) : 0.0;
+          S.ratio[s] = ratio;
+          S.sweeps[s] = sweep;
+          if (!(ratio >= a.rtol) || sweep == max_refine || !(ratio == ratio)) {
+            S.flags[s] |= F_DONE;
+          } else {
+            S.flags[s] |= F_INNER;
+            S.rho[s] = r64;
+            S.rho_first[s] = r64;
+          }
+        }
+      }
+    }
+    __syncthreads();
+    for (int it = 0;; ++it) {
+      // ---- P1: q = A p; sums and constraint functionals
+      clear_next();
+      zero_local();
+      if (it == 0) {
+        for (int s = 0; s < K; ++s)
+          if ((S.flags[s] & F_INNER) && leader(u0 + s) && tid == 0) atomicAdd(&a.cnt[ph % 3], 1);
+      }
+      __syncthreads();
+      for (long long c = c0 + tid; c < c1; c += L3_THREADS) {
+        Col<T> cl;
+        col_of(c, cl);
+        if (!(S.flags[cl.slot] & F_INNER)) continue;
+        const size_t ub = (size_t)cl.u * a.nv + cl.kx + (size_t)W * cl.ky;
+        const size_t mb = (size_t)cl.pt * a.nv + cl.kx + (size_t)W * cl.ky;
+        const uint8_t *lab = a.labels + (size_t)cl.pt * n * n * n;
+        const T *kap = a.kapT + (size_t)cl.pt * n * n * n;
+        T v[3][3][3], k[2][2][2];
+        load_plane9(v[0], a.p, ub, W);
+        load_plane9(v[1], a.p, ub + W2, W);
+        load_kplane(k[0], kap, cl.kx, cl.ky, 0, n);
+        int lo[2][2], up[2][2];
+        load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
+        ColBins<T, NCN> bz, bq;
+        bz.reset();
+        bq.reset();
+        bz.zb = bq.zb = 0;
+        T pq = 0, zq = 0, qmq = 0, rz = 0;
+        double *sb = S.bins + cl.slot * 2 * nc;
+        const T hT = (T)a.h;
+        for (int kz = 1; kz < n; ++kz) {
+          load_plane9(v[2], a.p, ub + W2 * (kz + 1), W);
+          load_kplane(k[1], kap, cl.kx, cl.ky, kz, n);
+          load_lplane(up, lab, cl.kx, cl.ky, kz, n, a.N - 1);
+          const size_t o = ub + W2 * kz;
+          const T q = hT * q1_apply3d<T>(v, k);
+          a.q[o] = q;
+          const T mi = a.minvT[mb + W2 * kz];
+          const T r = a.r[o];
+          const T z = mi * r, qm = mi * q;
+          pq += v[1][1][1] * q;
+          zq += z * q;
+          qmq += q * qm;
+          rz += r * z;
+          bz.add(lo, z);
+          bq.add(lo, qm);
+          if (kz % m == 0) {
+            bz.flush(sb, cl.kx, cl.ky, m, P, nq);
+            bq.flush(sb + nc, cl.kx, cl.ky, m, P, nq);
+            bz.zb = bq.zb = kz / m;
+          }
+          bz.add(up, z);
+          bq.add(up, qm);
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+              v[0][i][j] = v[1][i][j];
+              v[1][i][j] = v[2][i][j];
+            }
+#pragma unroll
+          for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+              k[0][i][j] = k[1][i][j];
+              lo[i][j] = up[i][j];
+            }
+        }
+        bz.flush(sb, cl.kx, cl.ky, m, P, nq);
+        bq.flush(sb + nc, cl.kx, cl.ky, m, P, nq);
+        double *ss = S.sums + cl.slot * 8;
+        atomicAdd(&ss[0], (double)pq);
+        atomicAdd(&ss[1], (double)zq);
+        atomicAdd(&ss[2], (double)qmq);
+        atomicAdd(&ss[3], (double)rz);
+      }
+      __syncthreads();
+      push_local(2 * nc);
+      sync();
+      if (it == 0 && *(volatile int *)&a.cnt[(ph + 2) % 3] == 0) {
+        finished = true;
+        break;
+      }
+
+      // ---- P2: scalars, lambda, updates
+      clear_next();
+      {
+        const double *rb = rbuf();
+        for (int s = 0; s < K; ++s) {
+          if (!(S.flags[s] & F_INNER)) continue;
+          const int u = u0 + s, pt = u / R;
+          const double *acc = rb + (size_t)u * NACC;
+          const double alpha = S.rho[s] / acc[0];
+          // c = Ct z - alpha Ct M^-1 q into the shared bins of the slot, lambda = S^-1 c
+          for (int i = tid; i < nc; i += L3_THREADS)
+            S.bins[s * 2 * nc + i] = acc[NACC_S + i] - alpha * acc[NACC_S + nc + i];
+          __syncthreads();
+          const T *Si = a.SinvT + (size_t)pt * nc * nc;
+          for (int i = tid; i < nc; i += L3_THREADS) {
+            T l = 0;
+            for (int j = 0; j < nc; ++j) l += Si[(size_t)j * nc + i] * (T)S.bins[s * 2 * nc + j];
+            S.vec[s * nc + i] = (double)l;
+          }
+          __syncthreads();
+          if (tid == 0) {
+            double lc = 0.0;
+            for (int i = 0; i < nc; ++i) lc += S.vec[s * nc + i] * S.bins[s * 2 * nc + i];
+            const double rn = acc[3] - 2.0 * alpha * acc[1] + alpha * alpha * acc[2] - lc;
+            S.alpha[s] = alpha;
+            S.beta[s] = rn / S.rho[s];
+            S.iters[s] += 1;
+            const bool bad = !(acc[0] > 0.0) || !(rn == rn);
+            if (bad) {
+              S.flags[s] = (S.flags[s] & ~F_INNER) | F_DONE | F_BREAK;
+            } else {
+              S.rho[s] = rn;
+              if (!(rn >= (double)a.tol * (double)a.tol * S.rho_first[s]) ||
+                  it + 1 >= a.max_iter)
+                S.flags[s] |= 8;  // last update of this sweep
+            }
+          }
+          __syncthreads();
+        }
+      }
+      for (long long c = c0 + tid; c < c1; c += L3_THREADS) {
+        Col<T> cl;
+        col_of(c, cl);
+        const int f = S.flags[cl.slot];
+        if (!(f & F_INNER)) continue;
+        const size_t ub = (size_t)cl.u * a.nv + cl.kx + (size_t)W * cl.ky;
+        const size_t mb = (size_t)cl.pt * a.nv + cl.kx + (size_t)W * cl.ky;
+        const uint8_t *lab = a.labels + (size_t)cl.pt * n * n * n;
+        const double *vec = S.vec + cl.slot * nc;
+        const T al = (T)S.alpha[cl.slot], be = (T)S.beta[cl.slot];
+        int lo[2][2], up[2][2];
+        load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
+        for (int kz = 1; kz < n; ++kz) {
+          load_lplane(up, lab, cl.kx, cl.ky, kz, n, a.N - 1);
+          const size_t o = ub + W2 * kz;
+          const T p = a.p[o];
+          a.d[o] += al * p;
+          const T r = a.r[o] - al * a.q[o] - (T)ctt_node(vec, lo, up, cl.kx, cl.ky, kz, m, P, nq);
+          a.r[o] = r;
+          if (!(f & 8)) a.p[o] = a.minvT[mb + W2 * kz] * r + be * p;
+#pragma unroll
+          for (int i = 0; i < 2; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) lo[i][j] = up[i][j];
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        for (int s = 0; s < K; ++s) {
+          if (!(S.flags[s] & F_INNER)) continue;
+          if (S.flags[s] & 8) {
+            S.flags[s] &= ~(F_INNER | 8);
+          } else if (leader(u0 + s)) {
+            atomicAdd(&a.cnt[ph % 3], 1);
+          }
+        }
+      }
+      __syncthreads();
+      sync();
+      if (*(volatile int *)&a.cnt[(ph + 2) % 3] == 0) break;
+    }
+  }
+
+  // per-unit records from the leader CTA
+  __syncthreads();
+  if (tid == 0) {
+    for (int s = 0; s < K; ++s) {
+      const int u = u0 + s;
+      if (!leader(u)) continue;
+      a.iters[u] = S.iters[s];
+      a.sweeps[u] = S.sweeps[s];
+      a.ratio[u] = S.ratio[s];
+      a.status[u] = (S.flags[s] & F_BREAK) ? 1 : 0;
+    }
+  }
+}
+
+template <typename T, int NCN>
+cudaError_t launch3(const Level3Args<T> &a0, cudaStream_t st) {
+  Level3Args<T> a = a0;
+  const long long cpu = (long long)(a.n - 1) * (a.n - 1);
+  const long long total = (long long)a.npts * a.R * cpu;
+  int dev = 0, sms = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  // slots per CTA: a range of C columns touches at most ceil(C / cpu) + 1 units
+  auto smem_for = [&](int kmax) {
+    return (size_t)kmax * (sizeof(double) * (8 + 3 * a.nc + 6) + sizeof(int) * 3) + 64;
+  };
+  int occ = 0;
+  int grid = 0;
+  for (int kmax = 2; kmax <= 64; kmax *= 2) {
+    const size_t smem = smem_for(kmax);
+    e = cudaFuncSetAttribute(k_level3d<T, NCN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_level3d<T, NCN>, L3_THREADS, smem);
+    if (e != cudaSuccess) return e;
+    if (occ < 1) return cudaErrorInvalidConfiguration;
+    grid = occ * sms;
+    long long per = (total + grid - 1) / grid;
+    per = ((per + L3_THREADS - 1) / L3_THREADS) * L3_THREADS;
+    const long long need = (per + cpu - 1) / cpu + 1;
+    if (need <= kmax) {
+      a.kmax = kmax;
+      a.cols_per_cta = per;
+      grid = (int)((total + per - 1) / per);
+      void *args[] = {&a};
+      return cudaLaunchCooperativeKernel((const void *)k_level3d<T, NCN>, dim3(grid),
+                                         dim3(L3_THREADS), args, smem, st);
+    }
+  }
+  return cudaErrorInvalidConfiguration;
+}
+
+}  // namespace
+
+template <typename T>
+cudaError_t launch_level3d(const Level3Args<T> &a, cudaStream_t st) {
+  if (a.nc > MCH_MAX_NC3 || a.n < 2 || a.n % a.P || a.m != a.n / a.P) return cudaErrorInvalidValue;
+  if (a.N <= 2) return launch3<T, 2>(a, st);
+  return launch3<T, 4>(a, st);
+}
+
+template cudaError_t launch_level3d<float>(const Level3Args<float> &, cudaStream_t);
+template cudaError_t launch_level3d<double>(const Level3Args<double> &, cudaStream_t);
+
+}  // namespace mch

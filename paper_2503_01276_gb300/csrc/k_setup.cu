@@ -100,10 +100,12 @@ __global__ void __launch_bounds__(SN_THREADS) k_setup_nodes(SetupArgs a, int sli
       const double dinv =
           fast_rcp((kap[eSW] + kap[eSE] + kap[eNW] + kap[eNE]) * (2.0 / 3.0));
       mv[col + W * ky] = dinv;
-      const int b0 = lab[eSW] * nq + ((ky - 1) / m) * P + (kx - 1) / m;
-      const int b1 = lab[eSE] * nq + ((ky - 1) / m) * P + kx / m;
-      const int b2 = lab[eNW] * nq + (ky / m) * P + (kx - 1) / m;
-      const int b3 = lab[eNE] * nq + (ky / m) * P + kx / m;
+      // labels of the neighbouring slice are not validated here: clamp them (an invalid
+      // label is reported by that slice)
+      const int b0 = min((int)lab[eSW], N - 1) * nq + ((ky - 1) / m) * P + (kx - 1) / m;
+      const int b1 = min((int)lab[eSE], N - 1) * nq + ((ky - 1) / m) * P + kx / m;
+      const int b2 = min((int)lab[eNW], N - 1) * nq + (ky / m) * P + (kx - 1) / m;
+      const int b3 = min((int)lab[eNE], N - 1) * nq + (ky / m) * P + kx / m;
       const unsigned key = (unsigned)b0 | ((unsigned)b1 << 8) | ((unsigned)b2 << 16) |
                            ((unsigned)b3 << 24);
       if (key != sig) {

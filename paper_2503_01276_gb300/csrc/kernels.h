@@ -19,9 +19,12 @@ struct SetupArgs {
   double *minv;           // [pt][nv] 1 / diag(A) at interior nodes (0 elsewhere)
   int nv;
   double *Sacc;           // [pt][nc][nc] scratch accumulator of S
-  double *bacc;           // [pt][nc][3] scratch: element count, centroid sums per row
+  double *bacc;           // [pt][nc][d+1] scratch: element count, centroid sums per row
+  float *kap32;           // 3D only: [pt][n^3] FP32 copy of kappa, or null
+  float *minv32;          // 3D only: [pt][nv] FP32 copy of M^-1, or null
 };
 cudaError_t launch_setup2d(const SetupArgs &a, cudaStream_t st);
+cudaError_t launch_setup3d(const SetupArgs &a, cudaStream_t st);
 
 // Persistent level solve (k_level.cuh): for every (point, function) unit, FP64 refinement
 // steps around inner projected-PCG sweeps, all on chip; writes the FP64 solution x.
@@ -44,6 +47,7 @@ struct LevelArgs {
   double rtol;            // refinement tolerance
   int max_refine;         // inner sweeps
   double *lam;            // [pt*R][nc] final multipliers (b - A x = Ct^T lam), or null
+  const double *bnorm;    // [pt*R] b'M^-1 b (reference floor of the stopping test), or null
 };
 template <typename T>
 cudaError_t launch_level2d(const LevelArgs<T> &a, cudaStream_t st);
@@ -60,6 +64,10 @@ struct ApplyArgs {
   double *y;              // [pt][R][nv]
 };
 cudaError_t launch_apply2d(const ApplyArgs &a, cudaStream_t st);
+
+// out[unit] = sum_k b[unit][k]^2 minv[pt][k] over nv entries (units = npts * R), FP64.
+cudaError_t launch_bnorm(int npts, int R, int nv, const double *b, const double *minv,
+                         double *out, cudaStream_t st);
 
 // out_coarse = scale * P^T y_fine (restriction by the transpose of the nested bilinear
 // prolongation), coarse grid n_c = n_f / rho, rho in {2, 4, 8}.
@@ -85,9 +93,58 @@ struct ChildArgs {
 };
 cudaError_t launch_child_fine2d(const ChildArgs &a, cudaStream_t st);
 
-// E[pt][r][s] += alpha * 1/2 sum_k (X_r Y_s + Y_r X_s), R in {3, 6, 9, 12}.
+// E[pt][r][s] += alpha * 1/2 sum_k (X_r Y_s + Y_r X_s), R in {3, 4, 6, 8, 9, 12}.
 cudaError_t launch_gram(int npts, int R, int nv, const double *X, const double *Y,
                         double alpha, double *E, cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------
+// 3D (k3d.cuh conventions: (n+1)^3 lattice, nv = nv3_of(n))
+
+// Persistent cooperative level solve (k_level3d.cu). Vectors stream through global memory;
+// x and d must be zero and p must have zero boundary entries on entry.
+template <typename T>
+struct Level3Args {
+  int npts, R, n, P, N, nc, nv, m;
+  const double *kappa;    // [pt][n^3]
+  const T *kapT;          // [pt][n^3] inner-precision kappa
+  const uint8_t *labels;  // [pt][n^3]
+  const T *SinvT;         // [pt][nc][nc]
+  const double *Sinv64;   // [pt][nc][nc]
+  const double *minv64;   // [pt][nv]
+  const T *minvT;         // [pt][nv]
+  const double *g;        // [pt][nc][R]
+  const double *b;        // [unit][nv] or null
+  double *x;              // [unit][nv]
+  double *r64;            // [unit][nv] scratch
+  T *p, *r, *d, *q;       // [unit][nv] scratch
+  double *acc;            // [3][unit][8 + 2 nc] scratch, zero on entry
+  int *cnt;               // [3] scratch, zero on entry
+  int *iters, *sweeps;    // [unit]
+  double *ratio;          // [unit]
+  int *status;            // [unit]
+  float tol;
+  int max_iter;
+  double rtol;
+  int max_refine;
+  double *lam;            // [unit][nc] or null
+  double h;
+  long long cols_per_cta; // set by the launcher
+  int kmax;               // set by the launcher
+  const double *bnorm;    // [unit] b'M^-1 b (reference floor of the stopping test), or null
+};
+template <typename T>
+cudaError_t launch_level3d(const Level3Args<T> &a, cudaStream_t st);
+
+// y = A(kappa_c prolonged) x + cb * b on an n-grid, kappa on the (n / rho)-grid.
+cudaError_t launch_apply3d(const ApplyArgs &a, double h, cudaStream_t st);
+// phi[pt][r] = sum_t w_t Phi_t[r] on the level-1 lattice.
+cudaError_t launch_interp3d(const ChildArgs &a, cudaStream_t st);
+// y = A_1 phi (child kappa prolonged to the level-1 grid) and g -= s * C_1 phi.
+cudaError_t launch_fine_apply3d(const ChildArgs &a, double hf, cudaStream_t st);
+cudaError_t launch_restrict3d(int npts, int R, int nf, int rho, const double *yf, int nvf,
+                              double scale, double *outc, int nvc, cudaStream_t st);
+cudaError_t launch_prolong_add3d(int npts, int R, int nf, int rho, const double *xc, int nvc,
+                                 double *phif, int nvf, cudaStream_t st);
 
 // Backward pass kernels (k_adjoint.cu).
 struct AdjArgs {
@@ -109,5 +166,8 @@ struct AdjArgs {
 cudaError_t launch_adj_combine2d(const AdjArgs &a, cudaStream_t st);
 cudaError_t launch_adj_grad2d(const AdjArgs &a, cudaStream_t st);
 cudaError_t launch_adj_seed2d(const AdjArgs &a, cudaStream_t st);
+cudaError_t launch_adj_combine3d(const AdjArgs &a, cudaStream_t st);
+cudaError_t launch_adj_grad3d(const AdjArgs &a, double hf, cudaStream_t st);
+cudaError_t launch_adj_seed3d(const AdjArgs &a, double hf, cudaStream_t st);
 
 }  // namespace mch

@@ -59,7 +59,10 @@ def test_descriptor_validation_without_gpu(mch):
     assert lib.mch_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
     bad = mch.desc_from_workload(wl, n_cont=7)
     assert lib.mch_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
-    d3 = mch.desc_from_workload(mi.workload("channel3d_9x9x9_L3"))
+    # 3D: up to three continua (12 cell functions); grids with at least 2 elements per period
+    d3 = mch.desc_from_workload(mi.workload("channel3d_9x9x9_L3"), n_cont=4, periods=2)
+    assert lib.mch_create(ctypes.byref(d3), None, ctypes.byref(h)) == 8
+    d3 = mch.desc_from_workload(mi.workload("channel3d_9x9x9_L3"), periods=16)
     assert lib.mch_create(ctypes.byref(d3), None, ctypes.byref(h)) == 8
     bad = mch.desc_from_workload(wl, point_batch=-1)
     assert lib.mch_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
