@@ -337,6 +337,12 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     rhs_per_step = sum(s.num_points(l) for l in range(1, L + 1)) * s.R
 
+    # launch shapes of the level solves, chosen by the library's autotuner on this workload
+    tiles = []
+    for lev in range(1, L + 1):
+        v, ms = s.autotune_level(lev, *med_dev[lev - 1])
+        tiles.append(v)
+
     def step(device_inputs=True):
         for lev in range(1, L + 1):
             k, lb = (med_dev if device_inputs else med_host)[lev - 1]
@@ -449,7 +455,8 @@ def main():
             "ms_per_step": float(np.mean(step_ms)), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-            "config": dict(_config(wl, args.precision), rhs_per_step=rhs_per_step),
+            "config": dict(_config(wl, args.precision), rhs_per_step=rhs_per_step,
+                           level_tiles=tiles),
             "roofline": roofline, "cpu_baseline": cpu, "plain_fp64_per_point": plain,
             "e2e": {"value": e2e_value, "unit": "RHS/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},

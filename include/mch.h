@@ -159,8 +159,8 @@ mch_status mch_effective_coeffs(mch_handle *h, int level, double *E, int32_t *it
                                 double *relres);
 
 /* Copies the level's cell functions on the level-1 grid, [n_points][R][(n_fine+1)^d] FP64
- * (node lattice including the zero boundary, x fastest), to `phi` (host or device). Needs
- * keep_parents = 1 or a level that has children. */
+ * (node lattice including the zero boundary, x fastest), to `phi` (host or device). With
+ * keep_parents = 0 the cell functions are recomputed first if they were freed. */
 mch_status mch_cell_functions(mch_handle *h, int level, double *phi);
 
 /* Enables (1) or disables (0) CUDA-event timing of the phases of mch_solve_level (adds
@@ -170,11 +170,30 @@ mch_status mch_set_timing(mch_handle *h, int enable);
 /* Statistics of the last mch_solve_level call on `level` (host struct). */
 mch_status mch_level_stats_get(const mch_handle *h, int level, mch_level_stats *out);
 
+/* Launch shape of the 2D mixed-precision level solve (no counterpart in the paper; a GPU
+ * tuning parameter). Shape 0 is the default; `count` shapes exist for the level's grid, and
+ * a shape is valid when its rows per thread divide the sub-block size n / P. Results do not
+ * depend on the shape beyond rounding. MCH_ERR_UNSUPPORTED for an invalid shape (and for
+ * any shape other than 0 in 3D or in FP64 mode). */
+mch_status mch_set_level_variant(mch_handle *h, int level, int variant);
+mch_status mch_get_level_variant(const mch_handle *h, int level, int *variant, int *count);
+
+/* Autotuner: solves `level` (as mch_solve_level, same arguments and ordering rules) once
+ * with every valid launch shape, keeps the one whose level solve was fastest (CUDA events on
+ * the handle's stream) and solves once more with it, so the level's results are those of a
+ * plain mch_solve_level. If the environment variable MCH_TUNE_CACHE names a file, a shape
+ * recorded there for the same (d, grid, P, N, precision, points) is used without timing, and
+ * a newly timed choice is appended to it. `best` and `best_ms` (optional) receive the chosen
+ * shape and its level-solve time (0 when taken from the cache). */
+mch_status mch_autotune_level(mch_handle *h, int level, const double *kappa,
+                              const uint8_t *labels, int *best, double *best_ms);
+
 /* Gradient of a scalar loss of the effective coefficients with respect to kappa of every
  * element of every point of every level (adjoint of the constrained solves and of the
  * interpolation, derived from the energy form of Eq. phi_abstract). dL_dE[n-1] points to
  * [n_points][R][R] FP64, dL_dkappa[n-1] to [n_points][n^d] FP64 (host or device), for
- * n = 1..L. Requires every level solved with keep_parents = 1. */
+ * n = 1..L. Requires every level solved; with keep_parents = 0 the cell functions are
+ * recomputed from the level-grid solutions first. */
 mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const *dL_dkappa);
 
 /* Size of the fixed device buffer used by mch_direct_noalloc (32 MiB per GPU that loads the

@@ -55,6 +55,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "mch_create": (C.c_int, [C.POINTER(MchDesc), P, C.POINTER(P)]),
         "mch_plan_level": (C.c_int, [C.POINTER(MchDesc), C.c_int, C.POINTER(C.c_int), P, P, P, P]),
         "mch_level_num_points": (C.c_int, [P, C.c_int]),
+        "mch_set_level_variant": (C.c_int, [P, C.c_int, C.c_int]),
+        "mch_get_level_variant": (C.c_int, [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "mch_autotune_level": (C.c_int, [P, C.c_int, P, P, C.POINTER(C.c_int),
+                                         C.POINTER(C.c_double)]),
         "mch_level_n_elem": (C.c_int, [P, C.c_int]),
         "mch_level_points": (C.c_int, [P, C.c_int, P]),
         "mch_level_parents": (C.c_int, [P, C.c_int, P, P, P]),
@@ -202,6 +206,25 @@ class Solver:
             return st
         self._check(st, "mch_solve_level")
         return st
+
+    def set_variant(self, level: int, variant: int):
+        """Launch shape of the level's 2D mixed-precision solve (0 = default)."""
+        self._check(_LIB.mch_set_level_variant(self._h, level, variant), "mch_set_level_variant")
+
+    def variant(self, level: int):
+        """(current launch shape, number of shapes for the level's grid)."""
+        v, c = C.c_int(), C.c_int()
+        self._check(_LIB.mch_get_level_variant(self._h, level, C.byref(v), C.byref(c)),
+                    "mch_get_level_variant")
+        return v.value, c.value
+
+    def autotune_level(self, level: int, kappa, labels):
+        """Times every valid launch shape on this level, keeps the fastest and solves with it
+        (mch_autotune_level). Returns (shape, level-solve ms)."""
+        b, ms = C.c_int(), C.c_double()
+        self._check(_LIB.mch_autotune_level(self._h, level, _ptr(kappa), _ptr(labels),
+                                            C.byref(b), C.byref(ms)), "mch_autotune_level")
+        return b.value, ms.value
 
     def effective_coeffs(self, level: int, E=None, iters=None, relres=None):
         if E is None:

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -44,6 +45,7 @@ struct Level {
   double *V = nullptr;            // [pt][R][nvf] backward seeds (levels with children)
   double **par_V = nullptr;       // [pt][slots] parents' seed blocks (levels > 1)
   bool solved = false;
+  int variant = 0;                // launch shape of the 2D mixed level solve
   mch_level_stats stats{};
 };
 
@@ -58,6 +60,8 @@ struct mch_handle {
   // scratch shared by the levels (solved one after another)
   double *yfine = nullptr, *yc = nullptr;
   double *bnorm = nullptr;  // [unit] b'M^-1 b of the current correction or adjoint problem
+  // 2D mixed precision: level-1-grid vectors (cell functions, A_1 I) are float-float planes
+  bool ffs = false;
   // 3D level-solve scratch: inner vectors, FP64 residual, rotating accumulators, counters
   void *s3p = nullptr, *s3r = nullptr, *s3d = nullptr, *s3q = nullptr;
   double *s3r64 = nullptr, *s3acc = nullptr;
@@ -173,7 +177,7 @@ cudaError_t launch_child(mch_handle *h, Level &L, double *g, int *nl = nullptr) 
                h->yfine, g, 1.0 / rho_pow(h, L.rho)};
   if (d.dim == 2) {
     if (nl) *nl = 1;
-    return launch_child_fine2d(ca, h->st);
+    return launch_child_fine2d(ca, h->ffs, h->st);
   }
   if (nl) *nl = 2;
   cudaError_t e = launch_interp3d(ca, h->st);
@@ -183,13 +187,17 @@ cudaError_t launch_child(mch_handle *h, Level &L, double *g, int *nl = nullptr) 
 
 cudaError_t launch_prolong(mch_handle *h, Level &L) {
   if (h->d.dim == 2)
-    return launch_prolong_add2d(L.npts, h->R, h->d.n_fine, L.rho, L.x, L.nv, L.phi, L.nvf, h->st);
+    return launch_prolong_add2d(L.npts, h->R, h->d.n_fine, L.rho, L.x, L.nv, L.phi, L.nvf, h->st,
+                                h->ffs);
   return launch_prolong_add3d(L.npts, h->R, h->d.n_fine, L.rho, L.x, L.nv, L.phi, L.nvf, h->st);
 }
 
-cudaError_t launch_restrict(mch_handle *h, Level &L, const double *yf, double scale, double *out) {
+// yf is a level-1-grid vector in the handle's storage (ffs) or, for the backward seeds, FP64
+cudaError_t launch_restrict(mch_handle *h, Level &L, const double *yf, double scale, double *out,
+                            bool ffs) {
   if (h->d.dim == 2)
-    return launch_restrict2d(L.npts, h->R, h->d.n_fine, L.rho, yf, L.nvf, scale, out, L.nv, h->st);
+    return launch_restrict2d(L.npts, h->R, h->d.n_fine, L.rho, yf, L.nvf, scale, out, L.nv, h->st,
+                             ffs);
   return launch_restrict3d(L.npts, h->R, h->d.n_fine, L.rho, yf, L.nvf, scale, out, L.nv, h->st);
 }
 
@@ -299,8 +307,9 @@ cudaError_t restore_phi(mch_handle *h) {
     if (!L.solved) continue;
     cudaError_t e;
     if (l == 0) {
-      e = cudaMemcpyAsync(L.phi, L.x, (size_t)L.npts * R * L.nv * sizeof(double),
-                          cudaMemcpyDeviceToDevice, h->st);
+      e = h->ffs ? launch_to_ff(L.npts * R, L.x, L.nv, L.phi, L.nvf, L.nv, h->st)
+                 : cudaMemcpyAsync(L.phi, L.x, (size_t)L.npts * R * L.nv * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, h->st);
     } else {
       e = launch_child(h, L, L.gI);
       if (e == cudaSuccess) e = launch_prolong(h, L);
@@ -369,6 +378,7 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
   h->R = d.n_cont * (1 + d.dim);
   h->nq = nq;
   h->nc = nc;
+  h->ffs = d.dim == 2 && d.precision == MCH_MIXED;
   h->slots = 1 << d.dim;
 
   std::vector<LevelPlan> plans;
@@ -571,8 +581,8 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
     CK(cudaMemsetAsync(L.E, 0, np * R * R * sizeof(double), st), "zero E");
     int nl = 0;
     CK(launch_child(h, L, L.gI, &nl), "child fine");
-    CK(launch_gram((int)np, R, L.nvf, L.phi, h->yfine, inv_vol, L.E, st), "gram I");
-    CK(launch_restrict(h, L, h->yfine, -1.0, L.b), "restrict");
+    CK(launch_gram((int)np, R, L.nvf, L.phi, h->yfine, inv_vol, L.E, st, h->ffs), "gram I");
+    CK(launch_restrict(h, L, h->yfine, -1.0, L.b, h->ffs), "restrict");
     CK(launch_bnorm((int)np, R, L.nv, L.b, L.minv, h->bnorm, st), "b norm");
     h->launches += nl + 3;
     g = L.gI;
@@ -611,7 +621,7 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
                           L.Sinv64 + p0 * nc * nc, L.minv + p0 * L.nv, g + p0 * nc * R, bb,
                           L.x + u0 * L.nv, L.iters + u0, L.sweeps + u0, L.ratio + u0,
                           L.ustat + u0, (float)d.inner_tol, max_iter, d.rtol, d.max_refine, lam,
-                          bvec ? h->bnorm + u0 : nullptr};
+                          bvec ? h->bnorm + u0 : nullptr, L.variant};
       CK(launch_level2d<float>(la, st), "level fp32");
     }
     ++h->launches;
@@ -626,7 +636,9 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
   CK(launch_gram((int)np, R, L.nv, L.x, h->yc, inv_vol, L.E, st), "gram");
   h->launches += 2;
   if (li == 0) {
-    CK(cudaMemcpyAsync(L.phi, L.x, np * R * L.nv * sizeof(double), cudaMemcpyDeviceToDevice, st),
+    CK(h->ffs ? launch_to_ff((int)(np * R), L.x, L.nv, L.phi, L.nvf, L.nv, st)
+              : cudaMemcpyAsync(L.phi, L.x, np * R * L.nv * sizeof(double),
+                                cudaMemcpyDeviceToDevice, st),
        "phi copy");
   } else {
     CK(launch_prolong(h, L), "prolong");
@@ -741,9 +753,25 @@ mch_status mch_cell_functions(mch_handle *h, int level, double *phi) {
   const size_t rows = (size_t)L.npts * h->R;
   const bool dev = is_device_ptr(phi);
   if (!dev) h->d2h += (long long)(row * rows);
-  CK(cudaMemcpy2DAsync(phi, row, L.phi, (size_t)L.nvf * sizeof(double), row, rows,
-                       dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st),
-     "copy phi");
+  if (h->ffs) {
+    // float-float planes -> FP64, through a temporary device buffer for host destinations
+    const int len = (int)(row / sizeof(double));
+    double *dst = phi, *tmp = nullptr;
+    if (!dev) {
+      CK(dalloc(h, &tmp, rows * (size_t)len), "cell functions buffer");
+      dst = tmp;
+    }
+    CK(launch_from_ff((int)rows, L.phi, L.nvf, dst, len, len, h->st), "convert phi");
+    if (!dev) {
+      CK(cudaMemcpyAsync(phi, tmp, rows * row, cudaMemcpyDeviceToHost, h->st), "copy phi");
+      CK(cudaStreamSynchronize(h->st), "sync");
+      dfree(h, tmp);
+    }
+  } else {
+    CK(cudaMemcpy2DAsync(phi, row, L.phi, (size_t)L.nvf * sizeof(double), row, rows,
+                         dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, h->st),
+       "copy phi");
+  }
   CK(cudaStreamSynchronize(h->st), "sync");
   return MCH_OK;
 }
@@ -758,6 +786,83 @@ mch_status mch_set_timing(mch_handle *h, int enable) {
   }
   h->timing = enable != 0;
   return MCH_OK;
+}
+
+mch_status mch_set_level_variant(mch_handle *h, int level, int variant) {
+  if (!valid_level(h, level)) return set_err(h, MCH_ERR_ARG, "bad level");
+  Level &L = h->lv[level - 1];
+  const bool fp64 = h->d.precision == MCH_FP64;
+  if (variant != 0 && (h->d.dim != 2 || !level2d_variant_ok(L.n, h->d.periods, fp64, variant)))
+    return set_err(h, MCH_ERR_UNSUPPORTED, "launch shape not valid for this level");
+  L.variant = variant;
+  return MCH_OK;
+}
+
+mch_status mch_get_level_variant(const mch_handle *h, int level, int *variant, int *count) {
+  if (!valid_level(h, level)) return MCH_ERR_ARG;
+  const Level &L = h->lv[level - 1];
+  if (variant) *variant = L.variant;
+  if (count)
+    *count = h->d.dim == 2 ? level2d_variant_count(L.n, h->d.precision == MCH_FP64) : 1;
+  return MCH_OK;
+}
+
+mch_status mch_autotune_level(mch_handle *h, int level, const double *kappa,
+                              const uint8_t *labels, int *best, double *best_ms) {
+  if (!valid_level(h, level) || !kappa || !labels) return set_err(h, MCH_ERR_ARG, "bad argument");
+  Level &L = h->lv[level - 1];
+  const mch_desc &d = h->d;
+  const bool fp64 = d.precision == MCH_FP64;
+  const int count = d.dim == 2 ? level2d_variant_count(L.n, fp64) : 1;
+  char key[160];
+  snprintf(key, sizeof key, "mch-tune %d %d %d %d %s %d", d.dim, L.n, d.periods, d.n_cont,
+           fp64 ? "fp64" : "mixed", L.npts);
+  const char *cache = getenv("MCH_TUNE_CACHE");
+  int chosen = -1;
+  double chosen_ms = 0.0;
+  if (cache && *cache) {
+    if (FILE *f = fopen(cache, "r")) {
+      char line[256];
+      const size_t kl = strlen(key);
+      while (fgets(line, sizeof line, f)) {
+        int v = -1;
+        if (strncmp(line, key, kl) == 0 && line[kl] == ' ' && sscanf(line + kl, "%d", &v) == 1 &&
+            v >= 0 && v < count && (v == 0 || level2d_variant_ok(L.n, d.periods, fp64, v)))
+          chosen = v;
+      }
+      fclose(f);
+    }
+  }
+  if (chosen < 0 && count > 1) {
+    const bool timing = h->timing;
+    mch_status st = mch_set_timing(h, 1);
+    if (st != MCH_OK) return st;
+    double best_t = 1e300;
+    for (int v = 0; v < count; ++v) {
+      if (v != 0 && !level2d_variant_ok(L.n, d.periods, fp64, v)) continue;
+      L.variant = v;
+      if (mch_solve_level(h, level, kappa, labels) != MCH_OK) continue;
+      const double t = L.stats.pcg_ms;
+      if (t < best_t) {
+        best_t = t;
+        chosen = v;
+      }
+    }
+    h->timing = timing;
+    if (chosen < 0) chosen = 0;
+    chosen_ms = best_t < 1e300 ? best_t : 0.0;
+    if (cache && *cache) {
+      if (FILE *f = fopen(cache, "a")) {
+        fprintf(f, "%s %d %.4f\n", key, chosen, chosen_ms);
+        fclose(f);
+      }
+    }
+  }
+  if (chosen < 0) chosen = 0;
+  L.variant = chosen;
+  if (best) *best = chosen;
+  if (best_ms) *best_ms = chosen_ms;
+  return mch_solve_level(h, level, kappa, labels);
 }
 
 mch_status mch_level_stats_get(const mch_handle *h, int level, mch_level_stats *out) {
@@ -839,7 +944,7 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
     if (seeds) {
       // adjoint constrained solve with right-hand side P^T V and zero targets
       if (L.rho > 1) {
-        CK(launch_restrict(h, L, L.V, 1.0, L.b), "restrict seeds");
+        CK(launch_restrict(h, L, L.V, 1.0, L.b, false), "restrict seeds");
       } else {
         CK(cudaMemcpyAsync(L.b, L.V, np * R * nvf * sizeof(double), cudaMemcpyDeviceToDevice, st),
            "copy seeds");
@@ -863,14 +968,14 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
                             L.labels, L.Sinv32, L.Sinv64, L.minv, h->gzero, L.b, h->yc,
                             h->bw_iters, h->bw_sweeps, h->bw_ratio, h->bw_status,
                             (float)d.inner_tol, max_iter, d.rtol, d.max_refine, h->lamadj,
-                            h->bnorm};
+                            h->bnorm, L.variant};
         CK(launch_level2d<float>(la, st), "adjoint fp32");
       }
     }
     AdjArgs aa{(int)np, R, d.n_fine, ilog2(L.rho), nvf, L.nv, nc, ilog2(d.n_fine / P), ilog2(P),
                h->slots, inv_vol, 1.0 / rho_pow(h, L.rho), h->Wd, L.phi,
                seeds ? h->yc : nullptr, L.lam, seeds ? h->lamadj : nullptr, L.kappa, L.labels,
-               L.V, h->psi1, h->psi2, h->dk, L.par_V, L.par_w};
+               L.V, h->psi1, h->psi2, h->dk, L.par_V, L.par_w, h->ffs ? 1 : 0};
     if (d3) {
       CK(launch_adj_combine3d(aa, st), "adjoint combine");
       CK(launch_adj_grad3d(aa, hf, st), "adjoint gradient");

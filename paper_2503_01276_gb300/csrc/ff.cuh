@@ -1,0 +1,101 @@
+// Float-float ("double-word") arithmetic: a value is the unevaluated sum hi + lo of two
+// floats with |lo| <= ulp(hi)/2, about 48 significant bits (relative rounding ~ 2^-47).
+//
+// On this GPU an FP64 FMA runs at about 1/64 of the FP32 rate and an FP64 -> FP32
+// conversion at about twice the FP64 FMA rate, so FP64-bound work on vectors kept in this
+// format (two float planes of the same size as one FP64 vector) runs on the FP32 pipes.
+//
+// Building blocks (error-free transformations):
+//   two_sum       Knuth's branch-free exact sum: s + e == a + b exactly.
+//   fast_two_sum  Dekker's exact sum for |a| >= |b| (or a == 0).
+//   two_prod      exact product with one FMA: p + e == a * b exactly.
+// Word operations follow the double-word algorithms of Joldes, Muller and Popescu
+// ("Tight and rigorous error bounds for basic building blocks of double-word arithmetic",
+// ACM TOMS 2017): the accurate sum of two double-words (relative error <= 3u^2) and the
+// product with one or two FMAs (relative error <= 5u^2 / 4u^2), u = 2^-24.
+//
+// Storage: a vector of nv entries occupies the space of nv doubles as a hi plane [nv] followed
+// by a lo plane [nv].
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace mch {
+
+struct ff {
+  float h, l;
+};
+
+// The _rn intrinsics are never contracted into FMAs, which would break exactness.
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ ff ff_from(double d) {
+  const float h = (float)d;
+  return ff{h, (float)(d - (double)h)};
+}
+__device__ __forceinline__ double ff_to(ff a) { return (double)a.h + (double)a.l; }
+__device__ __forceinline__ ff ff_of(float f) { return ff{f, 0.f}; }
+
+__device__ __forceinline__ ff operator+(ff a, ff b) {
+  float s, e, t, f;
+  two_sum(a.h, b.h, s, e);
+  two_sum(a.l, b.l, t, f);
+  e = __fadd_rn(e, t);
+  fast_two_sum(s, e, s, e);
+  e = __fadd_rn(e, f);
+  fast_two_sum(s, e, s, e);
+  return ff{s, e};
+}
+__device__ __forceinline__ ff operator-(ff a) { return ff{-a.h, -a.l}; }
+__device__ __forceinline__ ff operator-(ff a, ff b) { return a + (-b); }
+
+__device__ __forceinline__ ff operator*(ff a, ff b) {
+  const float p = __fmul_rn(a.h, b.h);
+  float e = __fmaf_rn(a.h, b.h, -p);
+  e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+  float s, t;
+  fast_two_sum(p, e, s, t);
+  return ff{s, t};
+}
+__device__ __forceinline__ ff operator*(ff a, float b) {
+  const float p = __fmul_rn(a.h, b);
+  float e = __fmaf_rn(a.h, b, -p);
+  e = __fmaf_rn(a.l, b, e);
+  float s, t;
+  fast_two_sum(p, e, s, t);
+  return ff{s, t};
+}
+__device__ __forceinline__ ff operator*(float b, ff a) { return a * b; }
+__device__ __forceinline__ ff &operator+=(ff &a, ff b) { return a = a + b; }
+__device__ __forceinline__ ff &operator-=(ff &a, ff b) { return a = a - b; }
+
+// acc += p with one two_sum on the high words (the cheaper "sloppy" double-word sum): error a
+// few units of 2^-47 of |acc| + |p|, enough for long reductions of mostly same-sign terms.
+__device__ __forceinline__ void ff_acc(ff &acc, ff p) {
+  float s, e;
+  two_sum(acc.h, p.h, s, e);
+  e = __fadd_rn(e, __fadd_rn(acc.l, p.l));
+  fast_two_sum(s, e, acc.h, acc.l);
+}
+
+// plane access: vector v (index of a whole vector) of a batch with stride nv entries
+__device__ __forceinline__ ff ff_load(const double *base, size_t v, int nv, int k) {
+  const float *p = reinterpret_cast<const float *>(base) + v * 2 * (size_t)nv;
+  return ff{p[k], p[nv + k]};
+}
+__device__ __forceinline__ void ff_store(double *base, size_t v, int nv, int k, ff x) {
+  float *p = reinterpret_cast<float *>(base) + v * 2 * (size_t)nv;
+  p[k] = x.h;
+  p[nv + k] = x.l;
+}
+
+}  // namespace mch

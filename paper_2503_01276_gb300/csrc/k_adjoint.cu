@@ -13,11 +13,17 @@
 // (Ct_1 is the fine-grid constraint operator in the library's scaling; rho^-2 converts the
 // level-n multipliers to it.)
 #include "common.cuh"
+#include "ff.cuh"
 #include "kernels.h"
 
 namespace mch {
 
 namespace {
+
+// cell function entry k of vector v (FP64 or float-float storage)
+__device__ __forceinline__ double phi_at(const AdjArgs &a, size_t v, int k) {
+  return a.ffs ? ff_to(ff_load(a.phi, v, a.nvf, k)) : a.phi[v * a.nvf + k];
+}
 
 // Psi' and Psi at every fine node of every point.
 template <int R>
@@ -35,7 +41,7 @@ __global__ void k_adj_combine2d(AdjArgs a) {
     for (int s = 0; s < R; ++s) wh[r * R + s] = (Wp[r * R + s] + Wp[s * R + r]) * a.inv_vol;
   double phi[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) phi[r] = a.phi[((size_t)pt * R + r) * a.nvf + k];
+  for (int r = 0; r < R; ++r) phi[r] = phi_at(a, (size_t)pt * R + r, k);
   // bilinear weights of P mu at this fine node
   const int bx = min(fx >> lgr, ncg - 1), by = min(fy >> lgr, ncg - 1);
   const double ir = 1.0 / rho;  // exact: rho is a power of two
@@ -74,7 +80,9 @@ __global__ void k_adj_grad2d(AdjArgs a) {
 #pragma unroll
       for (int s = 0; s < R; ++s) {
         const size_t o = ((size_t)pt * R + s) * a.nvf + k;
-        const double p0 = a.phi[o], p1 = a.phi[o + 1], p2 = a.phi[o + Wf], p3 = a.phi[o + Wf + 1];
+        const size_t v = (size_t)pt * R + s;
+        const double p0 = phi_at(a, v, k), p1 = phi_at(a, v, k + 1), p2 = phi_at(a, v, k + Wf),
+                     p3 = phi_at(a, v, k + Wf + 1);
         const double q0 = a.psi2[o], q1 = a.psi2[o + 1], q2 = a.psi2[o + Wf], q3 = a.psi2[o + Wf + 1];
         // unit-square Q1 element matrix times the corner values (corners 0 1 / 2 3, 0 and
         // 3 opposite): 1/6 (4 v_a - v_edge - v_edge - 2 v_opposite)

@@ -1,4 +1,4 @@
-// Level-1-grid (fine) work of a child level and the Gram reductions, FP64.
+// Level-1-grid (fine) work of a child level and the Gram reductions.
 //
 // Sec. 3.3, Eqs. (PhiXiI), (phiXiI_all): a point of level n > 1 starts from the
 // interpolation I = sum_t c_t Phi_t of its parents' cell functions on the level-1 grid.
@@ -14,67 +14,112 @@
 // k_gram2d reduces 1/2 sum_k (X_r Y_s + Y_r X_s) for every pair r <= s of a point with
 // the pair sums in registers, adding into E.
 // k_restrict2d forms b = scale * P^T y; k_prolong_add2d adds P x to the fine functions.
+//
+// Every kernel is a template over the storage of the level-1-grid vectors: FP64 (the FP64
+// mode) or float-float planes (ff.cuh; the mixed mode), whose arithmetic runs on the FP32
+// pipes. Level-grid vectors (x, b), kappa, the targets and E stay FP64.
 #include "common.cuh"
+#include "ff.cuh"
 #include "kernels.h"
 
 namespace mch {
 
 namespace {
 
+struct F64S {
+  using V = double;
+  __device__ static V ld(const double *b, size_t v, int nv, int k) { return b[v * nv + k]; }
+  __device__ static void st(double *b, size_t v, int nv, int k, V x) { b[v * nv + k] = x; }
+  __device__ static V from(double d) { return d; }
+  __device__ static double to(V x) { return x; }
+  __device__ static V zero() { return 0.0; }
+  __device__ static V shfl_xor(V v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
+  // acc += x * y + y' * x'
+  __device__ static void acc2(V &acc, V x, V y, V x2, V y2) { acc += x * y + x2 * y2; }
+};
+
+struct FFS {
+  using V = ff;
+  __device__ static V ld(const double *b, size_t v, int nv, int k) { return ff_load(b, v, nv, k); }
+  __device__ static void st(double *b, size_t v, int nv, int k, V x) { ff_store(b, v, nv, k, x); }
+  __device__ static V from(double d) { return ff_from(d); }
+  __device__ static double to(V x) { return ff_to(x); }
+  __device__ static V zero() { return ff{0.f, 0.f}; }
+  __device__ static V shfl_xor(V v, int o) {
+    return ff{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
+  }
+  __device__ static void acc2(V &acc, V x, V y, V x2, V y2) { ff_acc(acc, x * y + x2 * y2); }
+};
+
+template <class S>
+__device__ __forceinline__ typename S::V seg_sum_s(typename S::V v, int seg) {
+  for (int o = seg >> 1; o > 0; o >>= 1) v = v + S::shfl_xor(v, o);
+  return v;
+}
+
+// 2D Q1 stencil (h^{d-2} = 1): 1/6 [4 (a+b+c+d) x0 - (b+d) xE - (a+c) xW - (c+d) xN - (a+b) xS
+// - 2 (d xNE + c xNW + b xSE + a xSW)], a = SW, b = SE, c = NW, d = NE element kappa.
+template <typename V>
+__device__ __forceinline__ V q1v(V a, V b, V c, V d, V xSW, V xS, V xSE, V xW, V x0, V xE, V xNW,
+                                 V xN, V xNE, V sixth) {
+  const V t = (a + b + c + d) * x0 * 4.0f - (b + d) * xE - (a + c) * xW - (c + d) * xN -
+              (a + b) * xS - (d * xNE + c * xNW + b * xSE + a * xSW) * 2.0f;
+  return t * sixth;
+}
+
 constexpr int CF_THREADS = 256;
 constexpr int CF_BR = 16;   // fine rows per band
 
-template <int NC>
+template <int NC, class S>
 __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
+  using V = typename S::V;
   const int unit = blockIdx.y;
   const int pt = unit / a.R, r = unit % a.R;
   const int nf = a.nf, W = nf + 1, lgr = a.lgr, ncg = nf >> lgr;
   const int band = blockIdx.x;
   const int row_lo = band * CF_BR;                 // first own lattice row
   const int row_hi = min(row_lo + CF_BR, nf + 1);  // one past the last own row
-  __shared__ double tile[(CF_BR + 2) * 257];
+  __shared__ V tile[(CF_BR + 2) * 257];
   __shared__ double bins[MCH_MAX_NC];
   __shared__ const double *pp[4];
-  __shared__ double pw[4];
+  __shared__ V pw[4];
   const int tid = threadIdx.x;
   if (tid < a.slots) {
-    pw[tid] = a.par_w[pt * a.slots + tid];
+    pw[tid] = S::from(a.par_w[pt * a.slots + tid]);
     pp[tid] = a.par_ptr[pt * a.slots + tid];
   }
   for (int t = tid; t < a.nc; t += CF_THREADS) bins[t] = 0.0;
   __syncthreads();
 
   // I on rows row_lo-1 .. row_lo+CF_BR (rows outside the lattice are zero)
-  const size_t off = (size_t)r * a.nvf;
   for (int t = tid; t < (CF_BR + 2) * W; t += CF_THREADS) {
     const int row = row_lo - 1 + t / W, col = t % W;
-    double v = 0.0;
+    V v = S::zero();
     if (row >= 0 && row <= nf) {
       const int k = col + W * row;
       for (int s = 0; s < a.slots; ++s)
-        if (pw[s] != 0.0) v += pw[s] * pp[s][off + k];
+        if (pp[s]) v += pw[s] * S::ld(pp[s], r, a.nvf, k);
     }
     tile[t] = v;
   }
   __syncthreads();
 
   const double *kc = a.kappa_c + (size_t)pt * ncg * ncg;
-  double *phi = a.phi + (size_t)unit * a.nvf;
-  double *y = a.y + (size_t)unit * a.nvf;
+  const V sixth = S::from(1.0 / 6.0);
   for (int t = tid; t < (row_hi - row_lo) * W; t += CF_THREADS) {
     const int row = row_lo + t / W, col = t % W;
     const int k = col + W * row;
-    const double *tr = tile + (row - row_lo + 1) * W + col;
-    phi[k] = tr[0];
-    double v = 0.0;
+    const V *tr = tile + (row - row_lo + 1) * W + col;
+    S::st(a.phi, unit, a.nvf, k, tr[0]);
+    V v = S::zero();
     if (row > 0 && row < nf && col > 0 && col < nf) {
       const int e0x = (col - 1) >> lgr, e1x = col >> lgr;
       const int e0y = (row - 1) >> lgr, e1y = row >> lgr;
-      v = q1_apply(kc[e0x + ncg * e0y], kc[e1x + ncg * e0y], kc[e0x + ncg * e1y],
-                   kc[e1x + ncg * e1y], tr[-W - 1], tr[-W], tr[-W + 1], tr[-1], tr[0], tr[1],
-                   tr[W - 1], tr[W], tr[W + 1]);
+      v = q1v<V>(S::from(kc[e0x + ncg * e0y]), S::from(kc[e1x + ncg * e0y]),
+                 S::from(kc[e0x + ncg * e1y]), S::from(kc[e1x + ncg * e1y]), tr[-W - 1], tr[-W],
+                 tr[-W + 1], tr[-1], tr[0], tr[1], tr[W - 1], tr[W], tr[W + 1], sixth);
     }
-    y[k] = v;
+    S::st(a.y, unit, a.nvf, k, v);
   }
 
   // C_1 I on the band's element rows: element corner sums per (label, sub-block). Warp w
@@ -88,18 +133,18 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
     const int lgm = a.lgmf, m = 1 << lgm;
     const int seg = m < 32 ? m : 32;
     const uint8_t *lc = a.labels_c + (size_t)pt * ncg * ncg;
-    double acc[NC];
+    V acc[NC];
 #pragma unroll
-    for (int j = 0; j < NC; ++j) acc[j] = 0.0;
+    for (int j = 0; j < NC; ++j) acc[j] = S::zero();
     const int erow_hi = min(row_lo + CF_BR, nf);
     const int bx = ex >> lgm;
     auto flush = [&](int by) {
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
-        const double sj = seg_sum(acc[j], seg);
+        const double sj = S::to(seg_sum_s<S>(acc[j], seg));
         if ((lane & (seg - 1)) == 0 && sj != 0.0)
           atomicAdd(&bins[(j << (2 * a.lgP)) + (by << a.lgP) + bx], sj);
-        acc[j] = 0.0;
+        acc[j] = S::zero();
       }
     };
     // rows of one warp share ey, so the flush condition is uniform over the warp
@@ -110,11 +155,12 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
         if (by_cur >= 0) flush(by_cur);
         by_cur = by;
       }
-      const double *tr = tile + (ey - row_lo + 1) * W + ex;
-      const double sv = tr[0] + tr[1] + tr[W] + tr[W + 1];
+      const V *tr = tile + (ey - row_lo + 1) * W + ex;
+      const V sv = (tr[0] + tr[1]) + (tr[W] + tr[W + 1]);
       const int l = lc[(ex >> lgr) + ncg * (ey >> lgr)];
 #pragma unroll
-      for (int j = 0; j < NC; ++j) acc[j] += (l == j) ? sv : 0.0;
+      for (int j = 0; j < NC; ++j)
+        if (l == j) acc[j] += sv;
     }
     if (by_cur >= 0) flush(by_cur);
   }
@@ -125,37 +171,36 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
 
 constexpr int GR_THREADS = 256;
 
-template <int R>
+template <int R, class S>
 __global__ void __launch_bounds__(GR_THREADS) k_gram2d(int nv, int slices, const double *X,
                                                         const double *Y, double alpha, double *E) {
+  using V = typename S::V;
   constexpr int NP = R * (R + 1) / 2;
   const int pt = blockIdx.x;
   const int per = (nv + slices - 1) / slices;
   const int k0 = blockIdx.y * per, k1 = min(nv, k0 + per);
-  double acc[NP];
+  V acc[NP];
 #pragma unroll
-  for (int p = 0; p < NP; ++p) acc[p] = 0.0;
-  const double *Xp = X + (size_t)pt * R * nv;
-  const double *Yp = Y + (size_t)pt * R * nv;
+  for (int p = 0; p < NP; ++p) acc[p] = S::zero();
   for (int k = k0 + threadIdx.x; k < k1; k += GR_THREADS) {
-    double xv[R], yv[R];
+    V xv[R], yv[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      xv[r] = Xp[(size_t)r * nv + k];
-      yv[r] = Yp[(size_t)r * nv + k];
+      xv[r] = S::ld(X, (size_t)pt * R + r, nv, k);
+      yv[r] = S::ld(Y, (size_t)pt * R + r, nv, k);
     }
     int p = 0;
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
-      for (int s = r; s < R; ++s, ++p) acc[p] += xv[r] * yv[s] + yv[r] * xv[s];
+      for (int s = r; s < R; ++s, ++p) S::acc2(acc[p], xv[r], yv[s], yv[r], xv[s]);
   }
   __shared__ double red[GR_THREADS / 32][NP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    const double v = warp_sum(acc[p]);
-    if (lane == 0) red[w][p] = v;
+    const V v = seg_sum_s<S>(acc[p], 32);
+    if (lane == 0) red[w][p] = S::to(v);
   }
   __syncthreads();
   for (int p = threadIdx.x; p < NP; p += GR_THREADS) {
@@ -171,9 +216,10 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram2d(int nv, int slices, const
   }
 }
 
-template <int RHO>
+template <int RHO, class S>
 __global__ void k_restrict2d(int nf, const double *yf, int nvf, double scale, double *outc,
                              int nvc) {
+  using V = typename S::V;
   const int unit = blockIdx.y;
   const int ncg = nf / RHO, Wc = ncg + 1, Wf = nf + 1;
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -184,55 +230,78 @@ __global__ void k_restrict2d(int nf, const double *yf, int nvf, double scale, do
     o[k] = 0.0;
     return;
   }
-  const double *y = yf + (size_t)unit * nvf + (size_t)(Ky * RHO) * Wf + Kx * RHO;
-  double s = 0.0;
+  const int c0 = (Ky * RHO) * Wf + Kx * RHO;
+  V s = S::zero();
 #pragma unroll
   for (int dy = -(RHO - 1); dy <= RHO - 1; ++dy) {
-    double sx = 0.0;
+    V sx = S::zero();
 #pragma unroll
     for (int dx = -(RHO - 1); dx <= RHO - 1; ++dx)
-      sx += double(RHO - (dx < 0 ? -dx : dx)) * y[dy * Wf + dx];
-    s += double(RHO - (dy < 0 ? -dy : dy)) * sx;
+      sx += S::ld(yf, unit, nvf, c0 + dy * Wf + dx) * float(RHO - (dx < 0 ? -dx : dx));
+    s += sx * float(RHO - (dy < 0 ? -dy : dy));
   }
-  o[k] = scale * s * (1.0 / (RHO * RHO));
+  o[k] = scale * S::to(s) * (1.0 / (RHO * RHO));
 }
 
 // One thread per coarse cell: the cell's RHO x RHO fine nodes (lower-left corner included)
 // get the bilinear interpolant of the cell's four coarse values.
-template <int RHO>
+template <int RHO, class S>
 __global__ void k_prolong_add2d(int nf, const double *xc, int nvc, double *phif, int nvf) {
+  using V = typename S::V;
   const int unit = blockIdx.y;
   const int ncg = nf / RHO, Wc = ncg + 1, Wf = nf + 1;
   const int cell = blockIdx.x * blockDim.x + threadIdx.x;
   if (cell >= ncg * ncg) return;
   const int Kx = cell % ncg, Ky = cell / ncg;
   const double *x = xc + (size_t)unit * nvc + Kx + Wc * Ky;
-  const double x00 = x[0], x10 = x[1], x01 = x[Wc], x11 = x[Wc + 1];
-  double *f = phif + (size_t)unit * nvf + (size_t)(Ky * RHO) * Wf + Kx * RHO;
-  const double dl = x01 - x00, dr = x11 - x10;
+  const V x00 = S::from(x[0]), x10 = S::from(x[1]), x01 = S::from(x[Wc]), x11 = S::from(x[Wc + 1]);
+  const int f0 = (Ky * RHO) * Wf + Kx * RHO;
+  const V dl = x01 - x00, dr = x11 - x10;
 #pragma unroll
   for (int j = 0; j < RHO; ++j) {
-    const double ty = double(j) * (1.0 / RHO);
-    const double aj = x00 + ty * dl, bj = x10 + ty * dr;
-    const double dj = bj - aj;
+    const float ty = float(j) * (1.0f / RHO);  // exact: RHO is a power of two
+    const V aj = x00 + dl * ty, bj = x10 + dr * ty;
+    const V dj = bj - aj;
 #pragma unroll
-    for (int i = 0; i < RHO; ++i) f[j * Wf + i] += aj + double(i) * (1.0 / RHO) * dj;
+    for (int i = 0; i < RHO; ++i) {
+      const int k = f0 + j * Wf + i;
+      S::st(phif, unit, nvf, k, S::ld(phif, unit, nvf, k) + (aj + dj * (float(i) * (1.0f / RHO))));
+    }
   }
+}
+
+// FP64 <-> float-float planes, `count` vectors of nv entries (only the first `len` of each)
+__global__ void k_to_ff(const double *src, int nvs, double *dst, int nvd, int len) {
+  const int v = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= nvd) return;
+  ff_store(dst, v, nvd, k, ff_from(k < len ? src[(size_t)v * nvs + k] : 0.0));
+}
+__global__ void k_from_ff(const double *src, int nvs, double *dst, int nvd, int len) {
+  const int v = blockIdx.y;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= len) return;
+  dst[(size_t)v * nvd + k] = ff_to(ff_load(src, v, nvs, k));
 }
 
 }  // namespace
 
-cudaError_t launch_child_fine2d(const ChildArgs &a, cudaStream_t st) {
+cudaError_t launch_child_fine2d(const ChildArgs &a, bool ffs, cudaStream_t st) {
   if (a.nf < 32 || a.nf > 256) return cudaErrorInvalidValue;
   dim3 grid((a.nf + 1 + CF_BR - 1) / CF_BR, a.npts * a.R);
-  if (a.N <= 2) k_child_fine2d<2><<<grid, CF_THREADS, 0, st>>>(a);
-  else if (a.N == 3) k_child_fine2d<3><<<grid, CF_THREADS, 0, st>>>(a);
-  else k_child_fine2d<4><<<grid, CF_THREADS, 0, st>>>(a);
+#define CF_LAUNCH(NCV)                                                             \
+  (ffs ? (k_child_fine2d<NCV, FFS><<<grid, CF_THREADS, 0, st>>>(a), 0)            \
+       : (k_child_fine2d<NCV, F64S><<<grid, CF_THREADS, 0, st>>>(a), 0))
+  if (a.N <= 2) CF_LAUNCH(2);
+  else if (a.N == 3) CF_LAUNCH(3);
+  else CF_LAUNCH(4);
+#undef CF_LAUNCH
   return cudaGetLastError();
 }
 
-cudaError_t launch_gram(int npts, int R, int nv, const double *X, const double *Y,
-                        double alpha, double *E, cudaStream_t st) {
+template <class S>
+cudaError_t gram_s(int npts, int R, int nv, const double *X, const double *Y, double alpha,
+                   double *E, cudaStream_t st) {
   int slices = nv >= 8192 ? 8 : (nv >= 2048 ? 4 : 1);
   if (nv > 100000) {
     // 3D level-1 lattices: enough slices for every SM when the level has few points
@@ -241,40 +310,74 @@ cudaError_t launch_gram(int npts, int R, int nv, const double *X, const double *
   }
   dim3 grid(npts, slices);
   switch (R) {
-    case 3: k_gram2d<3><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
-    case 4: k_gram2d<4><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
-    case 8: k_gram2d<8><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
-    case 6: k_gram2d<6><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
-    case 9: k_gram2d<9><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
-    case 12: k_gram2d<12><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+    case 3: k_gram2d<3, S><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+    case 4: k_gram2d<4, S><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+    case 6: k_gram2d<6, S><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+    case 8: k_gram2d<8, S><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+    case 9: k_gram2d<9, S><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+    case 12: k_gram2d<12, S><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram(int npts, int R, int nv, const double *X, const double *Y,
+                        double alpha, double *E, cudaStream_t st, bool ffs) {
+  return ffs ? gram_s<FFS>(npts, R, nv, X, Y, alpha, E, st)
+             : gram_s<F64S>(npts, R, nv, X, Y, alpha, E, st);
+}
+
+template <class S>
+cudaError_t restrict_s(int npts, int R, int nf, int rho, const double *yf, int nvf, double scale,
+                       double *outc, int nvc, cudaStream_t st) {
+  const int Wc = nf / rho + 1;
+  dim3 grid((Wc * Wc + 255) / 256, npts * R);
+  switch (rho) {
+    case 2: k_restrict2d<2, S><<<grid, 256, 0, st>>>(nf, yf, nvf, scale, outc, nvc); break;
+    case 4: k_restrict2d<4, S><<<grid, 256, 0, st>>>(nf, yf, nvf, scale, outc, nvc); break;
+    case 8: k_restrict2d<8, S><<<grid, 256, 0, st>>>(nf, yf, nvf, scale, outc, nvc); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_restrict2d(int npts, int R, int nf, int rho, const double *yf, int nvf,
-                              double scale, double *outc, int nvc, cudaStream_t st) {
-  const int Wc = nf / rho + 1;
-  dim3 grid((Wc * Wc + 255) / 256, npts * R);
+                              double scale, double *outc, int nvc, cudaStream_t st, bool ffs) {
+  return ffs ? restrict_s<FFS>(npts, R, nf, rho, yf, nvf, scale, outc, nvc, st)
+             : restrict_s<F64S>(npts, R, nf, rho, yf, nvf, scale, outc, nvc, st);
+}
+
+template <class S>
+cudaError_t prolong_s(int npts, int R, int nf, int rho, const double *xc, int nvc, double *phif,
+                      int nvf, cudaStream_t st) {
+  const int ncg = nf / rho;
+  dim3 grid((ncg * ncg + 127) / 128, npts * R);
   switch (rho) {
-    case 2: k_restrict2d<2><<<grid, 256, 0, st>>>(nf, yf, nvf, scale, outc, nvc); break;
-    case 4: k_restrict2d<4><<<grid, 256, 0, st>>>(nf, yf, nvf, scale, outc, nvc); break;
-    case 8: k_restrict2d<8><<<grid, 256, 0, st>>>(nf, yf, nvf, scale, outc, nvc); break;
+    case 2: k_prolong_add2d<2, S><<<grid, 128, 0, st>>>(nf, xc, nvc, phif, nvf); break;
+    case 4: k_prolong_add2d<4, S><<<grid, 128, 0, st>>>(nf, xc, nvc, phif, nvf); break;
+    case 8: k_prolong_add2d<8, S><<<grid, 128, 0, st>>>(nf, xc, nvc, phif, nvf); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_prolong_add2d(int npts, int R, int nf, int rho, const double *xc, int nvc,
-                                 double *phif, int nvf, cudaStream_t st) {
-  const int ncg = nf / rho;
-  dim3 grid((ncg * ncg + 127) / 128, npts * R);
-  switch (rho) {
-    case 2: k_prolong_add2d<2><<<grid, 128, 0, st>>>(nf, xc, nvc, phif, nvf); break;
-    case 4: k_prolong_add2d<4><<<grid, 128, 0, st>>>(nf, xc, nvc, phif, nvf); break;
-    case 8: k_prolong_add2d<8><<<grid, 128, 0, st>>>(nf, xc, nvc, phif, nvf); break;
-    default: return cudaErrorInvalidValue;
-  }
+                                 double *phif, int nvf, cudaStream_t st, bool ffs) {
+  return ffs ? prolong_s<FFS>(npts, R, nf, rho, xc, nvc, phif, nvf, st)
+             : prolong_s<F64S>(npts, R, nf, rho, xc, nvc, phif, nvf, st);
+}
+
+cudaError_t launch_to_ff(int count, const double *src, int nvs, double *dst, int nvd, int len,
+                         cudaStream_t st) {
+  dim3 grid((nvd + 255) / 256, count);
+  k_to_ff<<<grid, 256, 0, st>>>(src, nvs, dst, nvd, len);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_from_ff(int count, const double *src, int nvs, double *dst, int nvd, int len,
+                           cudaStream_t st) {
+  dim3 grid((len + 255) / 256, count);
+  k_from_ff<<<grid, 256, 0, st>>>(src, nvs, dst, nvd, len);
   return cudaGetLastError();
 }
 

@@ -8,6 +8,7 @@ namespace mch {
 
 template <>
 cudaError_t launch_level2d<float>(const LevelArgs<float> &a, cudaStream_t st) {
+  if (a.variant != 0) return launch_level2d_alt(a, st);
   switch (a.n) {
     case 16: return launch_level_nc<float, 16, 16, 1, 1, 4>(a, st);
     case 32: return launch_level_nc<float, 32, 8, 4, 1, 3>(a, st);

@@ -48,10 +48,17 @@ struct LevelArgs {
   int max_refine;         // inner sweeps
   double *lam;            // [pt*R][nc] final multipliers (b - A x = Ct^T lam), or null
   const double *bnorm;    // [pt*R] b'M^-1 b (reference floor of the stopping test), or null
+  int variant;            // launch shape (0 = default; see level2d_variant_ok)
 };
 template <typename T>
 cudaError_t launch_level2d(const LevelArgs<T> &a, cudaStream_t st);
 bool level2d_supported(int n, int P, bool fp64);
+// Alternative launch shapes of the FP32-inner 2D level kernel (k_level_f32_alt.cu): number
+// of shapes for grid n (including the default, index 0), whether shape v is valid for
+// (n, P), and the launcher for v >= 1.
+int level2d_variant_count(int n, bool fp64);
+bool level2d_variant_ok(int n, int P, bool fp64, int v);
+cudaError_t launch_level2d_alt(const LevelArgs<float> &a, cudaStream_t st);
 
 // y = A(kappa) x + cb * b on an n-grid whose kappa lives on the (n/rho)-grid (piecewise
 // constant), for a batch of vectors; FP64.
@@ -69,14 +76,24 @@ cudaError_t launch_apply2d(const ApplyArgs &a, cudaStream_t st);
 cudaError_t launch_bnorm(int npts, int R, int nv, const double *b, const double *minv,
                          double *out, cudaStream_t st);
 
-// out_coarse = scale * P^T y_fine (restriction by the transpose of the nested bilinear
-// prolongation), coarse grid n_c = n_f / rho, rho in {2, 4, 8}.
-cudaError_t launch_restrict2d(int npts, int R, int nf, int rho, const double *yf, int nvf,
-                              double scale, double *outc, int nvc, cudaStream_t st);
+// Level-1-grid vectors are FP64, or float-float planes (ff.cuh) when `ffs` is set.
 
-// phi_fine += P x_coarse, rho in {2, 4, 8}.
+// out_coarse = scale * P^T y_fine (restriction by the transpose of the nested bilinear
+// prolongation), coarse grid n_c = n_f / rho, rho in {2, 4, 8}; out is FP64.
+cudaError_t launch_restrict2d(int npts, int R, int nf, int rho, const double *yf, int nvf,
+                              double scale, double *outc, int nvc, cudaStream_t st,
+                              bool ffs = false);
+
+// phi_fine += P x_coarse (x FP64), rho in {2, 4, 8}.
 cudaError_t launch_prolong_add2d(int npts, int R, int nf, int rho, const double *xc, int nvc,
-                                 double *phif, int nvf, cudaStream_t st);
+                                 double *phif, int nvf, cudaStream_t st, bool ffs = false);
+
+// `count` vectors: FP64 (stride nvs) -> float-float planes (stride nvd; entries >= len are 0),
+// and float-float planes (stride nvs) -> FP64 (stride nvd, first len entries).
+cudaError_t launch_to_ff(int count, const double *src, int nvs, double *dst, int nvd, int len,
+                         cudaStream_t st);
+cudaError_t launch_from_ff(int count, const double *src, int nvs, double *dst, int nvd, int len,
+                           cudaStream_t st);
 
 // Fine-grid work of a child level (k_child.cu): I = sum_t w_t Phi_t into phi, y = A_1 I, and
 // g -= s * C_1 I (g holds the targets on entry).
@@ -91,11 +108,11 @@ struct ChildArgs {
   double *g;                      // [pt][nc][R]
   double s;                       // rho^-2
 };
-cudaError_t launch_child_fine2d(const ChildArgs &a, cudaStream_t st);
+cudaError_t launch_child_fine2d(const ChildArgs &a, bool ffs, cudaStream_t st);
 
 // E[pt][r][s] += alpha * 1/2 sum_k (X_r Y_s + Y_r X_s), R in {3, 4, 6, 8, 9, 12}.
 cudaError_t launch_gram(int npts, int R, int nv, const double *X, const double *Y,
-                        double alpha, double *E, cudaStream_t st);
+                        double alpha, double *E, cudaStream_t st, bool ffs = false);
 
 // ---------------------------------------------------------------------------------------
 // 3D (k3d.cuh conventions: (n+1)^3 lattice, nv = nv3_of(n))
@@ -162,6 +179,7 @@ struct AdjArgs {
   double *dkappa;           // [pt][ncg^2]
   double *const *par_V;     // [pt][slots] parents' seed blocks
   const double *par_w;      // [pt][slots]
+  int ffs;                  // phi stored as float-float planes
 };
 cudaError_t launch_adj_combine2d(const AdjArgs &a, cudaStream_t st);
 cudaError_t launch_adj_grad2d(const AdjArgs &a, cudaStream_t st);
