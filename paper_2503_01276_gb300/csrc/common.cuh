@@ -124,6 +124,16 @@ __device__ __forceinline__ T ct_lambda(const Strip &s, int ky, int lSW, int lSE,
 // 2D Q1 stencil at a node from the four adjacent kappas (a = SW, b = SE, c = NW, d = NE;
 // h^{d-2} = 1 in 2D) and the 3x3 neighbourhood of x. Element matrix entries 2/3 (same node),
 // -1/6 (edge neighbour), -1/3 (opposite corner).
+// The same stencil for any value type with +, - and products by float (FP64 or float-float);
+// sixth = 1/6 in that type.
+template <typename V>
+__device__ __forceinline__ V q1v(V a, V b, V c, V d, V xSW, V xS, V xSE, V xW, V x0, V xE, V xNW,
+                                 V xN, V xNE, V sixth) {
+  const V t = (a + b + c + d) * x0 * 4.0f - (b + d) * xE - (a + c) * xW - (c + d) * xN -
+              (a + b) * xS - (d * xNE + c * xNW + b * xSE + a * xSW) * 2.0f;
+  return t * sixth;
+}
+
 template <typename T>
 __device__ __forceinline__ T q1_apply(T a, T b, T c, T d, T xSW, T xS, T xSE, T xW, T x0, T xE,
                                       T xNW, T xN, T xNE) {

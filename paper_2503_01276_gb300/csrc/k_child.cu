@@ -57,16 +57,6 @@ __device__ __forceinline__ typename S::V seg_sum_s(typename S::V v, int seg) {
   return v;
 }
 
-// 2D Q1 stencil (h^{d-2} = 1): 1/6 [4 (a+b+c+d) x0 - (b+d) xE - (a+c) xW - (c+d) xN - (a+b) xS
-// - 2 (d xNE + c xNW + b xSE + a xSW)], a = SW, b = SE, c = NW, d = NE element kappa.
-template <typename V>
-__device__ __forceinline__ V q1v(V a, V b, V c, V d, V xSW, V xS, V xSE, V xW, V x0, V xE, V xNW,
-                                 V xN, V xNE, V sixth) {
-  const V t = (a + b + c + d) * x0 * 4.0f - (b + d) * xE - (a + c) * xW - (c + d) * xN -
-              (a + b) * xS - (d * xNE + c * xNW + b * xSE + a * xSW) * 2.0f;
-  return t * sixth;
-}
-
 constexpr int CF_THREADS = 256;
 constexpr int CF_BR = 16;   // fine rows per band
 
