@@ -87,6 +87,10 @@ typedef struct {
                                solutions (interpolation + prolongation, no new solve) when
                                mch_backward, mch_cell_functions or a later mch_solve_level
                                needs them                                                   */
+  int interp;               /* parents of a point of level n > 1 (Sec. 3.3): 0 = vertices of
+                               the enclosing T_{n-1} cell with multilinear weights; 1 = the
+                               nearest point of S_1 with weight one (the paper's experiments:
+                               I_p = Phi_t, x_t in S_1; ties to the lower index)            */
   int point_batch;          /* points per constrained-solve launch: 0 = the whole level in
                                one persistent launch; k > 0 = at most k points per launch
                                (1 = one macropoint per launch, the unbatched comparator).

@@ -38,6 +38,7 @@ class Workload:
     contrast: float
     seed: int = 1
     precision: str = "mixed"  # "fp64" | "mixed"
+    interp: str = "multilinear"  # "multilinear" | "nearest1" (nearest point of S_1)
 
     @property
     def n_rhs(self) -> int:

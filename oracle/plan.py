@@ -49,7 +49,15 @@ def level_plan(wl):
         for pos, p in enumerate(pts):
             where[tuple(p)] = (n + 1, pos)
         parents = []
-        if n > 0:
+        if n > 0 and getattr(wl, "interp", "multilinear") == "nearest1":
+            # Sec. 3.3, the choice of the numerical experiments: I_p = Phi_t with x_t the
+            # nearest point of S_1 (= T_1), weight one; ties to the lower index
+            s1 = strides[0]
+            for p in pts:
+                q = tuple(int((i // s1) * s1 + (s1 if 2 * (i % s1) > s1 else 0)) for i in p)
+                lev, pos = where[q]
+                parents.append([(lev, pos, 1.0)])
+        elif n > 0:
             sp_ = strides[n - 1]
             for p in pts:
                 axes = []

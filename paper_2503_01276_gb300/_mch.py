@@ -32,7 +32,7 @@ class MchDesc(C.Structure):
                 ("periods", C.c_int), ("overs", C.c_int), ("rve_len", C.c_double),
                 ("precision", C.c_int), ("rtol", C.c_double), ("inner_tol", C.c_double),
                 ("max_iter", C.c_int), ("max_refine", C.c_int), ("keep_parents", C.c_int),
-                ("point_batch", C.c_int)]
+                ("interp", C.c_int), ("point_batch", C.c_int)]
 
 
 class MchLevelStats(C.Structure):
@@ -101,14 +101,16 @@ def _ptr(a) -> int:
 
 def make_desc(dim, n_cont, strides, eta, macro_n, n_fine, periods, rve_len, precision="mixed",
               rtol=0.0, inner_tol=0.0, max_iter=0, max_refine=0, keep_parents=1, overs=0,
-              point_batch=0):
+              point_batch=0, interp="multilinear"):
     arr = (C.c_int * len(strides))(*[int(s) for s in strides])
     d = MchDesc(dim=dim, n_cont=n_cont, n_levels=len(strides), eta=eta, macro_n=macro_n,
                 level_stride=C.cast(arr, C.POINTER(C.c_int)), n_fine=n_fine, periods=periods,
                 overs=overs, rve_len=rve_len,
                 precision=MCH_FP64 if precision == "fp64" else MCH_MIXED, rtol=rtol,
                 inner_tol=inner_tol, max_iter=max_iter, max_refine=max_refine,
-                keep_parents=keep_parents, point_batch=point_batch)
+                keep_parents=keep_parents, point_batch=point_batch,
+                interp={"multilinear": 0, "nearest1": 1}[interp] if isinstance(interp, str)
+                else int(interp))
     d._strides_keepalive = arr
     return d
 
@@ -116,7 +118,7 @@ def make_desc(dim, n_cont, strides, eta, macro_n, n_fine, periods, rve_len, prec
 def desc_from_workload(wl, **kw) -> MchDesc:
     args = dict(dim=wl.dim, n_cont=wl.n_cont, strides=wl.strides, eta=wl.eta,
                 macro_n=wl.macro_n, n_fine=wl.n_fine, periods=wl.periods, rve_len=wl.rve_len,
-                precision=wl.precision)
+                precision=wl.precision, interp=getattr(wl, "interp", "multilinear"))
     args.update(kw)
     return make_desc(**args)
 

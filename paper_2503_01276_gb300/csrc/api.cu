@@ -383,7 +383,7 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
 
   std::vector<LevelPlan> plans;
   std::string perr;
-  if (!build_plan(d.dim, d.macro_n, h->strides, d.n_fine, d.eta, plans, perr)) {
+  if (!build_plan(d.dim, d.macro_n, h->strides, d.n_fine, d.eta, plans, perr, d.interp)) {
     delete h;
     return MCH_ERR_ARG;
   }
@@ -491,7 +491,8 @@ mch_status mch_plan_level(const mch_desc *desc, int level, int *n_points, int32_
   std::vector<LevelPlan> plans;
   std::string err;
   if (desc->eta < 1 ||
-      !build_plan(desc->dim, desc->macro_n, strides, desc->n_fine, desc->eta, plans, err))
+      !build_plan(desc->dim, desc->macro_n, strides, desc->n_fine, desc->eta, plans, err,
+                  desc->interp))
     return MCH_ERR_ARG;
   const LevelPlan &L = plans[level - 1];
   *n_points = (int)L.points.size() / desc->dim;

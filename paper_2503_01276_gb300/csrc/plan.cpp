@@ -6,7 +6,8 @@
 namespace mch {
 
 bool build_plan(int dim, int macro_n, const std::vector<int> &strides, int n_fine, int eta,
-                std::vector<LevelPlan> &levels, std::string &err) {
+                std::vector<LevelPlan> &levels, std::string &err, int interp) {
+  if (interp != 0 && interp != 1) { err = "interp must be 0 or 1"; return false; }
   const int L = (int)strides.size();
   if (L < 1 || strides.back() != 1) { err = "the last level stride must be 1"; return false; }
   for (int i = 0; i + 1 < L; ++i)
@@ -49,6 +50,24 @@ bool build_plan(int dim, int macro_n, const std::vector<int> &strides, int n_fin
           lp.par_level.push_back(0);
           lp.par_pos.push_back(0);
           lp.par_w.push_back(0.0);
+        }
+        continue;
+      }
+      if (interp == 1) {
+        // nearest point of S_1 = T_1 (per axis: round to the stride, ties down)
+        const int s1 = strides[0];
+        long long pf = 0, mul = 1;
+        for (int a = 0; a < dim; ++a) {
+          const int lo = (idx[a] / s1) * s1, rem = idx[a] - lo;
+          pf += (long long)(2 * rem > s1 ? lo + s1 : lo) * mul;
+          mul *= macro_n;
+        }
+        auto it = where.find(pf);
+        if (it == where.end() || it->second.first != 1) { err = "internal: S_1 parent"; return false; }
+        for (int t = 0; t < slots; ++t) {
+          lp.par_level.push_back(t == 0 ? 1 : 0);
+          lp.par_pos.push_back(t == 0 ? it->second.second : 0);
+          lp.par_w.push_back(t == 0 ? 1.0 : 0.0);
         }
         continue;
       }

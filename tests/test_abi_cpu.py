@@ -37,10 +37,11 @@ def test_exports_every_declared_symbol(mch):
         assert hasattr(lib, nm), nm
 
 
+@pytest.mark.parametrize("interp", ["multilinear", "nearest1"])
 @pytest.mark.parametrize("name", ["channel2d_4x4_n32", "channel2d_17x17_L3", "incl2d_33x33_L4",
                                   "channel3d_9x9x9_L3", "channel2d_65x65_L3_adj"])
-def test_host_plan_matches_oracle(mch, name):
-    wl = mi.workload(name)
+def test_host_plan_matches_oracle(mch, name, interp):
+    wl = mi.workload(name, interp=interp)
     d = mch.desc_from_workload(wl)
     pl = plan.level_plan(wl)
     for lev in range(1, wl.n_levels + 1):

@@ -82,6 +82,18 @@ def test_hierarchy_small(name, n_fine, macro, strides, precision):
         assert (np.abs(phi - ref) / scale).max() < 1e-9, lev
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_hierarchy_nearest_s1(precision):
+    """The single-parent interpolation variant (nearest point of S_1, weight one)."""
+    wl = mi.small_workload("channel2d_17x17_L3", n_fine=64, macro_n=9, strides=(4, 2, 1),
+                           precision=precision, interp="nearest1")
+    s, Eg = _run_gpu(wl, rtol=1e-11)
+    Eo = _run_oracle(wl)
+    for lev in range(wl.n_levels):
+        err = block_rel_err(Eg[lev], Eo[lev]["E"], wl.n_cont, wl.dim)
+        assert err < 1e-9, (lev + 1, err)
+
+
 def test_host_buffers_match_device_buffers():
     """Host and device buffers give the same answer. Shared-memory reductions use atomics,
     so two runs agree to the solver tolerance rather than bit for bit."""

@@ -64,6 +64,27 @@ def test_level_plan_counts(name, counts):
 
 
 @pytest.mark.parametrize("name", ["channel2d_17x17_L3", "channel3d_9x9x9_L3"])
+def test_level_plan_nearest_s1(name):
+    """The single-parent variant (Sec. 3.3, I_p = Phi_t with x_t in S_1): one parent, on
+    level 1, weight one, at the smallest Euclidean distance over all of S_1 (brute force;
+    ties to the lexicographically smallest index along each axis)."""
+    wl = mi.workload(name, interp="nearest1")
+    pl = plan.level_plan(wl)
+    s1 = pl[0]["points"]
+    for n in range(1, len(pl)):
+        for p, par in zip(pl[n]["points"], pl[n]["parents"]):
+            assert len(par) == 1
+            lv, i, w = par[0]
+            assert lv == 1 and w == 1.0
+            d2 = np.sum((s1 - p) ** 2, axis=1)
+            best = np.flatnonzero(d2 == d2.min())
+            # among equidistant points the one with the smallest coordinates
+            cand = s1[best]
+            j = best[np.lexsort(cand.T[::-1])[0]]
+            assert i == j, (p, s1[i], s1[j])
+
+
+@pytest.mark.parametrize("name", ["channel2d_17x17_L3", "channel3d_9x9x9_L3"])
 def test_level_plan_parents(name):
     """Weights sum to one (Sec. 3.3), parents lie on earlier levels at distance
     below the T_{n-1} spacing (the dense property), and the weighted parent
