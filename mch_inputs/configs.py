@@ -39,6 +39,7 @@ class Workload:
     seed: int = 1
     precision: str = "mixed"  # "fp64" | "mixed"
     interp: str = "multilinear"  # "multilinear" | "nearest1" (nearest point of S_1)
+    overs: int = 0               # oversampling layers: R_p = central (P - 2 overs)^d periods
 
     @property
     def n_rhs(self) -> int:

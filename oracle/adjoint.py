@@ -28,8 +28,15 @@ import numpy as np
 from . import cell, fe
 
 
+def _check_stationary(wl):
+    # the envelope form of the level's own term holds only for R_p = Y+ (o = 0)
+    if getattr(wl, "overs", 0):
+        raise NotImplementedError("gradient with oversampling (o > 0) is not derived here")
+
+
 def forward(wl, plan, media_levels):
     """Forward pass keeping every point's solve result (Phi, Xi, beta, keep, E)."""
+    _check_stationary(wl)
     res = []
     for n, lev in enumerate(plan):
         ops = cell.LevelOps(wl, n + 1)
@@ -120,6 +127,7 @@ def backward_sampled(wl, plan, media_fn, weights):
     seeds, so the forward and reverse sweeps run over that closure alone (Algorithm 1
     restricted to it). media_fn(level, positions) -> (kappa, labels). Returns
     ({(level, position): dL/dkappa [n_n^d]}, loss)."""
+    _check_stationary(wl)
     R = wl.n_rhs
     fwd = cell.run_sampled(wl, plan, media_fn, list(weights))
     nf_nodes = fe.Grid(wl.dim, wl.n_fine, wl.rve_len).n_nodes

@@ -151,7 +151,7 @@ def run_hierarchy(wl, plan, media_levels, keep_phi=True, points=None):
                 I = np.zeros((ops.gf.n_nodes, R))
                 for (lv, pos, w) in lev["parents"][i]:
                     I += w * phis[lv - 1][pos].T
-            r = solve_point(ops, kap[i], lab[i], I)
+            r = solve_point(ops, kap[i], lab[i], I, overs=getattr(wl, "overs", 0))
             E[i] = r["E"]
             if Phi is not None:
                 Phi[i] = r["Phi"]
@@ -195,5 +195,5 @@ def run_sampled(wl, plan, media_fn, targets):
                 I = np.zeros((ops.gf.n_nodes, wl.n_rhs))
                 for (pl, pp, w) in plan[lv - 1]["parents"][i]:
                     I += w * out[(pl, pp)]["Phi"].T
-            out[(lv, i)] = solve_point(ops, kap[k], lab[k], I)
+            out[(lv, i)] = solve_point(ops, kap[k], lab[k], I, overs=getattr(wl, "overs", 0))
     return out

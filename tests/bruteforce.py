@@ -42,10 +42,17 @@ def el_id(e, n):
     return sum(e[a] * n ** a for a in range(len(e)))
 
 
-def dense_system(d, n, L, kappa, labels, N, P):
+def in_region(e, n, P, overs):
+    """Element e lies in the central (P - 2 overs)^d periods."""
+    m = n // P
+    return all(overs * m <= e[a] < (P - overs) * m for a in range(len(e)))
+
+
+def dense_system(d, n, L, kappa, labels, N, P, overs=0):
     """Dense A on all (n+1)^d nodes, constraint rows C (all (j,q) rows) and
     targets G (all rows), plus the interior mask. kappa/labels are flat with
-    x fastest."""
+    x fastest. With overs > 0 the centroids are taken over the central
+    (P - 2 overs)^d periods (over the whole RVE if a continuum is absent there)."""
     h = L / n
     cs, K = khat_closed_form(d)
     nn = (n + 1) ** d
@@ -54,15 +61,22 @@ def dense_system(d, n, L, kappa, labels, N, P):
     m = n // P
     C = np.zeros((N * nq, nn))
     vol = h ** d
-    # centroids over the whole RVE (o = 0)
     sums = np.zeros((N, d))
     cnt = np.zeros(N)
+    sums_all = np.zeros((N, d))
+    cnt_all = np.zeros(N)
     for e in itertools.product(range(n), repeat=d):
         eid = el_id(e, n)
         j = int(labels[eid])
         y = np.array([-L / 2 + (e[a] + 0.5) * h for a in range(d)])
-        sums[j] += y
-        cnt[j] += 1
+        sums_all[j] += y
+        cnt_all[j] += 1
+        if in_region(e, n, P, overs):
+            sums[j] += y
+            cnt[j] += 1
+    use = cnt > 0
+    sums = np.where(use[:, None], sums, sums_all)
+    cnt = np.where(use, cnt, cnt_all)
     cen = np.where(cnt[:, None] > 0, sums / np.maximum(cnt, 1)[:, None], 0.0)
     G = np.zeros((N * nq, N * (1 + d)))
     for e in itertools.product(range(n), repeat=d):
@@ -110,16 +124,29 @@ def kkt_solve(A, C, b, g):
     return sol[:n], sol[n:]
 
 
-def cell_E(d, n, L, kappa, labels, N, P):
-    """Level-1 effective coefficients by the dense KKT solve."""
-    A, C, G, mask = dense_system(d, n, L, kappa, labels, N, P)
+def cell_E(d, n, L, kappa, labels, N, P, overs=0):
+    """Level-1 effective coefficients by the dense KKT solve; with overs > 0 the energy is
+    integrated over the central (P - 2 overs)^d periods and divided by their volume."""
+    A, C, G, mask = dense_system(d, n, L, kappa, labels, N, P, overs)
     Ai = A[np.ix_(mask, mask)]
     Ci = C[:, mask]
     keep = np.abs(Ci).sum(axis=1) > 0
     x, beta = kkt_solve(Ai, Ci[keep], np.zeros((mask.sum(), G.shape[1])), G[keep])
     Phi = np.zeros((A.shape[0], G.shape[1]))
     Phi[mask] = x
-    return Phi.T @ A @ Phi / L ** d, Phi
+    if overs == 0:
+        return Phi.T @ A @ Phi / L ** d, Phi
+    h = L / n
+    cs, K = khat_closed_form(d)
+    Ar = np.zeros_like(A)
+    ne = 0
+    for e in itertools.product(range(n), repeat=d):
+        if not in_region(e, n, P, overs):
+            continue
+        ne += 1
+        ids = [node_id(tuple(e[a] + c[a] for a in range(d)), n) for c in cs]
+        Ar[np.ix_(ids, ids)] += kappa[el_id(e, n)] * h ** (d - 2) * K
+    return Phi.T @ Ar @ Phi / (ne * h ** d), Phi
 
 
 def child_E(d, nf, nc, L, kappa_c, labels_c, N, P, I):

@@ -128,6 +128,23 @@ def test_level1_matches_dense_kkt(name, n, d):
         assert _rel(r["Phi"], Phib.T) < 1e-10
 
 
+@pytest.mark.parametrize("d,n,P,overs", [(2, 16, 4, 1), (2, 32, 8, 2), (3, 8, 4, 1)])
+def test_oversampling_matches_dense_kkt(d, n, P, overs):
+    """Oversampling (R_p = central (P - 2o)^d periods): centroids over R_p, constraints on
+    every period, E integrated over R_p only, against the dense brute force."""
+    name = "channel2d_17x17_L3" if d == 2 else "channel3d_9x9x9_L3"
+    wl = _small(name, n_fine=n, macro_n=3, strides=(1,), periods=P)
+    pts = np.array([[1] * d])
+    kap, lab = mi.media(wl, pts, n)
+    r = cell.solve_point(cell.LevelOps(wl, 1), kap[0], lab[0], overs=overs)
+    Eb, Phib = bf.cell_E(d, n, wl.rve_len, kap[0], lab[0], wl.n_cont, P, overs)
+    assert _rel(r["E"], Eb) < RTOL
+    assert _rel(r["Phi"], Phib.T) < 1e-10
+    # R_p = Y+ for o = 0 is the plain level-1 problem
+    r0 = cell.solve_point(cell.LevelOps(wl, 1), kap[0], lab[0], overs=0)
+    assert _rel(r["E"], r0["E"]) > 1e-6
+
+
 def test_child_correction_matches_dense_kkt():
     """Level-2 correction problem (Eqs. phi_avar_corrector, phi_grad_corrector)
     against the dense fine-grid KKT with the coarse basis evaluated pointwise."""
