@@ -66,7 +66,11 @@ typedef struct {
   const int *level_stride;  /* [n_levels] stride of T_n in macro-index units, last = 1      */
   int n_fine;               /* elements per RVE side at level 1                             */
   int periods;              /* P: sub-blocks R_q per side; n_level / P must be >= 2         */
-  int overs;                /* oversampling layers o; only 0 is built (MCH_ERR_UNSUPPORTED) */
+  int overs;                /* oversampling layers o: E is integrated over R_p, the central
+                               (P - 2o)^d periods, with centroids c_mj over R_p (Sec. 2, Eqs.
+                               phi_grad, Bs_defi); constraints stay on every period. 2D only
+                               (3D: MCH_ERR_UNSUPPORTED); P - 2o >= 1; mch_backward returns
+                               MCH_ERR_UNSUPPORTED for o > 0                                */
   double rve_len;           /* l: RVE side length                                           */
   int precision;            /* MCH_MIXED (FP32 PCG inside FP64 refinement) or MCH_FP64      */
   double rtol;              /* stop when sqrt(r'M^-1 r / rho_ref) < rtol for the FP64

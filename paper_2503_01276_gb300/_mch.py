@@ -118,7 +118,8 @@ def make_desc(dim, n_cont, strides, eta, macro_n, n_fine, periods, rve_len, prec
 def desc_from_workload(wl, **kw) -> MchDesc:
     args = dict(dim=wl.dim, n_cont=wl.n_cont, strides=wl.strides, eta=wl.eta,
                 macro_n=wl.macro_n, n_fine=wl.n_fine, periods=wl.periods, rve_len=wl.rve_len,
-                precision=wl.precision, interp=getattr(wl, "interp", "multilinear"))
+                precision=wl.precision, interp=getattr(wl, "interp", "multilinear"),
+                overs=getattr(wl, "overs", 0))
     args.update(kw)
     return make_desc(**args)
 

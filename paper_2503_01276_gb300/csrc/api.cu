@@ -60,6 +60,9 @@ struct mch_handle {
   // scratch shared by the levels (solved one after another)
   double *yfine = nullptr, *yc = nullptr;
   double *bnorm = nullptr;  // [unit] b'M^-1 b of the current correction or adjoint problem
+  // oversampling (o > 0): A_1 I with kappa masked to R_p (level-1 grid), P^T of it (level
+  // grid), and the masked level kappa
+  double *yfineR = nullptr, *cR = nullptr, *kapR = nullptr;
   // 2D mixed precision: level-1-grid vectors (cell functions, A_1 I) are float-float planes
   bool ffs = false;
   // 3D level-solve scratch: inner vectors, FP64 residual, rotating accumulators, counters
@@ -174,7 +177,7 @@ cudaError_t launch_child(mch_handle *h, Level &L, double *g, int *nl = nullptr) 
   const mch_desc &d = h->d;
   ChildArgs ca{L.npts, h->R, d.n_fine, ilog2(L.rho), L.nvf, h->slots, ilog2(d.n_fine / d.periods),
                ilog2(d.periods), d.n_cont, h->nc, L.par_ptr, L.par_w, L.kappa, L.labels, L.phi,
-               h->yfine, g, 1.0 / rho_pow(h, L.rho)};
+               h->yfine, g, 1.0 / rho_pow(h, L.rho), h->yfineR, d.overs};
   if (d.dim == 2) {
     if (nl) *nl = 1;
     return launch_child_fine2d(ca, h->ffs, h->st);
@@ -360,7 +363,9 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
       (d.precision != MCH_FP64 && d.precision != MCH_MIXED) || d.rtol < 0 || d.inner_tol < 0 ||
       d.max_iter < 0 || d.max_refine < 0 || d.point_batch < 0)
     return MCH_ERR_ARG;
-  if (d.overs != 0) return MCH_ERR_UNSUPPORTED;
+  // oversampling: 2D only, at least one period in the integration region
+  if (d.overs < 0 || d.periods - 2 * d.overs < 1) return MCH_ERR_ARG;
+  if (d.overs != 0 && d.dim != 2) return MCH_ERR_UNSUPPORTED;
   const int nq = d.dim == 3 ? d.periods * d.periods * d.periods : d.periods * d.periods;
   const int nc = d.n_cont * nq;
   if (nc > (d.dim == 3 ? MCH_MAX_NC3 : MCH_MAX_NC)) return MCH_ERR_UNSUPPORTED;
@@ -476,6 +481,13 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
     ALLOC(h->bnorm, max_units);
   }
   if (max_fine) ALLOC(h->yfine, max_fine);
+  if (d.overs > 0) {
+    size_t max_el = 0;
+    for (const Level &L : h->lv) max_el = std::max(max_el, (size_t)L.npts * elems(d.dim, L.n));
+    if (max_fine) ALLOC(h->yfineR, max_fine);
+    ALLOC(h->cR, max_unit_nvc);
+    ALLOC(h->kapR, max_el);
+  }
 #undef ALLOC
   cudaError_t e = cudaStreamSynchronize(h->st);
   if (e != cudaSuccess) { mch_destroy(h); return MCH_ERR_CUDA; }
@@ -566,13 +578,16 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
   // ---- constraint data
   SetupArgs sa{(int)np, L.n, P, N, R, nc, d.rve_len / L.n, d.rve_len, L.kappa, L.labels,
                L.G, L.Sinv64, L.Sinv32, L.pstat, L.dropped, L.minv, L.nv, L.Sacc, L.bacc,
-               L.kap32, L.minv32};
+               L.kap32, L.minv32, d.overs};
   CK(mark(-1), "event");
   CK(d3 ? launch_setup3d(sa, st) : launch_setup2d(sa, st), "setup");
   h->launches += 2;
   CK(mark(0), "event");
 
-  const double inv_vol = 1.0 / (d3 ? d.rve_len * d.rve_len * d.rve_len : d.rve_len * d.rve_len);
+  // |R_p| = the central (P - 2 overs)^d periods (the whole RVE when overs = 0)
+  const double rlen = d.rve_len * (double)(P - 2 * d.overs) / P;
+  const double inv_vol = 1.0 / (d3 ? rlen * rlen * rlen : rlen * rlen);
+  const bool ovs = d.overs > 0;
   const double *g = L.G;
   const double *bvec = nullptr;
   if (li > 0) {
@@ -582,8 +597,14 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
     CK(cudaMemsetAsync(L.E, 0, np * R * R * sizeof(double), st), "zero E");
     int nl = 0;
     CK(launch_child(h, L, L.gI, &nl), "child fine");
-    CK(launch_gram((int)np, R, L.nvf, L.phi, h->yfine, inv_vol, L.E, st, h->ffs), "gram I");
+    CK(launch_gram((int)np, R, L.nvf, L.phi, ovs ? h->yfineR : h->yfine, inv_vol, L.E, st,
+                   h->ffs),
+       "gram I");
     CK(launch_restrict(h, L, h->yfine, -1.0, L.b, h->ffs), "restrict");
+    if (ovs) {
+      CK(launch_restrict(h, L, h->yfineR, 1.0, h->cR, h->ffs), "restrict R_p");
+      ++h->launches;
+    }
     CK(launch_bnorm((int)np, R, L.nv, L.b, L.minv, h->bnorm, st), "b norm");
     h->launches += nl + 3;
     g = L.gI;
@@ -631,7 +652,16 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
   CK(mark(2), "event");
 
   // ---- effective coefficients and the cell functions on the level-1 grid
+  // |Y| E = K_I + sym(Xi^T (A_n Xi - 2 b)); with oversampling every operator is restricted to
+  // R_p: |R_p| E = K_I,R + sym(Xi^T (A_n,R Xi + 2 P^T A_1,R I))
   ApplyArgs ac{(int)np, R, L.n, 1, L.nv, L.kappa, L.x, bvec, -2.0, h->yc};
+  if (ovs) {
+    CK(launch_mask_region2d((int)np, L.n, P, d.overs, L.kappa, h->kapR, st), "mask kappa");
+    ++h->launches;
+    ac.kappa = h->kapR;
+    ac.b = li > 0 ? h->cR : nullptr;
+    ac.cb = 2.0;
+  }
   CK(d3 ? launch_apply3d(ac, d.rve_len / L.n, st) : launch_apply2d(ac, st), "apply coarse");
   if (li == 0) CK(cudaMemsetAsync(L.E, 0, np * R * R * sizeof(double), st), "zero E");
   CK(launch_gram((int)np, R, L.nv, L.x, h->yc, inv_vol, L.E, st), "gram");
@@ -882,6 +912,10 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
     if (!h->lv[l].solved) return set_err(h, MCH_ERR_ORDER, "every level must be solved first");
     if (!dL_dE[l] || !dL_dkappa[l]) return set_err(h, MCH_ERR_ARG, "null gradient buffer");
   }
+  if (d.overs > 0)
+    return set_err(h, MCH_ERR_UNSUPPORTED,
+                   "gradient with oversampling: the level's own coefficients are not "
+                   "stationary in its cell functions; not built");
   cudaStream_t st = h->st;
   const int nvf = nvd(d.dim, d.n_fine);
   const bool d3 = d.dim == 3;

@@ -101,15 +101,30 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
     const int k = col + W * row;
     const V *tr = tile + (row - row_lo + 1) * W + col;
     S::st(a.phi, unit, a.nvf, k, tr[0]);
-    V v = S::zero();
+    V v = S::zero(), vR = S::zero();
     if (row > 0 && row < nf && col > 0 && col < nf) {
       const int e0x = (col - 1) >> lgr, e1x = col >> lgr;
       const int e0y = (row - 1) >> lgr, e1y = row >> lgr;
-      v = q1v<V>(S::from(kc[e0x + ncg * e0y]), S::from(kc[e1x + ncg * e0y]),
-                 S::from(kc[e0x + ncg * e1y]), S::from(kc[e1x + ncg * e1y]), tr[-W - 1], tr[-W],
-                 tr[-W + 1], tr[-1], tr[0], tr[1], tr[W - 1], tr[W], tr[W + 1], sixth);
+      const V kSW = S::from(kc[e0x + ncg * e0y]), kSE = S::from(kc[e1x + ncg * e0y]);
+      const V kNW = S::from(kc[e0x + ncg * e1y]), kNE = S::from(kc[e1x + ncg * e1y]);
+      v = q1v<V>(kSW, kSE, kNW, kNE, tr[-W - 1], tr[-W], tr[-W + 1], tr[-1], tr[0], tr[1],
+                 tr[W - 1], tr[W], tr[W + 1], sixth);
+      if (a.yR) {
+        // the same with kappa zero outside the integration region (period index of each
+        // adjacent fine element)
+        const int P = 1 << a.lgP, o = a.overs;
+        auto in = [&](int ex, int ey) {
+          const int px = ex >> a.lgmf, py = ey >> a.lgmf;
+          return px >= o && px < P - o && py >= o && py < P - o;
+        };
+        const V z = S::zero();
+        vR = q1v<V>(in(col - 1, row - 1) ? kSW : z, in(col, row - 1) ? kSE : z,
+                    in(col - 1, row) ? kNW : z, in(col, row) ? kNE : z, tr[-W - 1], tr[-W],
+                    tr[-W + 1], tr[-1], tr[0], tr[1], tr[W - 1], tr[W], tr[W + 1], sixth);
+      }
     }
     S::st(a.y, unit, a.nvf, k, v);
+    if (a.yR) S::st(a.yR, unit, a.nvf, k, vR);
   }
 
   // C_1 I on the band's element rows: element corner sums per (label, sub-block). Warp w

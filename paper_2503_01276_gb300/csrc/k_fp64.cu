@@ -61,6 +61,26 @@ __global__ void __launch_bounds__(256) k_bnorm(int R, int nv, const double *b, c
 
 }  // namespace
 
+namespace {
+
+__global__ void k_mask_region2d(int n, int P, int overs, const double *kappa, double *out) {
+  const int pt = blockIdx.y;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= n * n) return;
+  const int m = n / P, px = (e % n) / m, py = (e / n) / m;
+  const bool in = px >= overs && px < P - overs && py >= overs && py < P - overs;
+  out[(size_t)pt * n * n + e] = in ? kappa[(size_t)pt * n * n + e] : 0.0;
+}
+
+}  // namespace
+
+cudaError_t launch_mask_region2d(int npts, int n, int P, int overs, const double *kappa,
+                                 double *out, cudaStream_t st) {
+  dim3 grid((n * n + 255) / 256, npts);
+  k_mask_region2d<<<grid, 256, 0, st>>>(n, P, overs, kappa, out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bnorm(int npts, int R, int nv, const double *b, const double *minv,
                          double *out, cudaStream_t st) {
   k_bnorm<<<npts * R, 256, 0, st>>>(R, nv, b, minv, out);

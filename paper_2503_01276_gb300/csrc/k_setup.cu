@@ -146,16 +146,28 @@ __global__ void __launch_bounds__(SP_THREADS) k_setup_point(SetupArgs a) {
   for (int i = tid; i < 3 * nc; i += SP_THREADS) bs[i] = a.bacc[(size_t)pt * nc * 3 + i];
   __syncthreads();
 
-  // centroids c_mj over the whole RVE
+  // centroids c_mj over the integration region R_p (the central (P - 2 overs)^2 periods;
+  // the whole RVE when the continuum is absent there, or when overs = 0)
   if (tid < N) {
-    double c = 0, x = 0, y = 0;
+    double c = 0, x = 0, y = 0, ca = 0, xa = 0, ya = 0;
     for (int q = 0; q < nq; ++q) {
       const int b = tid * nq + q;
-      c += bs[3 * b];
-      x += bs[3 * b + 1];
-      y += bs[3 * b + 2];
+      const int qx = q % P, qy = q / P;
+      ca += bs[3 * b];
+      xa += bs[3 * b + 1];
+      ya += bs[3 * b + 2];
+      if (qx >= a.overs && qx < P - a.overs && qy >= a.overs && qy < P - a.overs) {
+        c += bs[3 * b];
+        x += bs[3 * b + 1];
+        y += bs[3 * b + 2];
+      }
     }
-    if (c == 0.0) atomicOr(&flags, 8);
+    if (ca == 0.0) atomicOr(&flags, 8);
+    if (c == 0.0) {
+      c = ca;
+      x = xa;
+      y = ya;
+    }
     cen[2 * tid] = c > 0 ? x / c : 0.0;
     cen[2 * tid + 1] = c > 0 ? y / c : 0.0;
   }

@@ -22,6 +22,7 @@ struct SetupArgs {
   double *bacc;           // [pt][nc][d+1] scratch: element count, centroid sums per row
   float *kap32;           // 3D only: [pt][n^3] FP32 copy of kappa, or null
   float *minv32;          // 3D only: [pt][nv] FP32 copy of M^-1, or null
+  int overs;              // 2D: centroids over the central (P - 2 overs)^2 periods
 };
 cudaError_t launch_setup2d(const SetupArgs &a, cudaStream_t st);
 cudaError_t launch_setup3d(const SetupArgs &a, cudaStream_t st);
@@ -72,6 +73,10 @@ struct ApplyArgs {
 };
 cudaError_t launch_apply2d(const ApplyArgs &a, cudaStream_t st);
 
+// out[pt][e] = kappa[pt][e] on elements of the central (P - 2 overs)^2 periods, else 0 (2D).
+cudaError_t launch_mask_region2d(int npts, int n, int P, int overs, const double *kappa,
+                                 double *out, cudaStream_t st);
+
 // out[unit] = sum_k b[unit][k]^2 minv[pt][k] over nv entries (units = npts * R), FP64.
 cudaError_t launch_bnorm(int npts, int R, int nv, const double *b, const double *minv,
                          double *out, cudaStream_t st);
@@ -107,6 +112,8 @@ struct ChildArgs {
   double *y;                      // [pt][R][nvf]
   double *g;                      // [pt][nc][R]
   double s;                       // rho^-2
+  double *yR;                     // 2D oversampling: A_1 I with kappa zero outside R_p, or null
+  int overs;
 };
 cudaError_t launch_child_fine2d(const ChildArgs &a, bool ffs, cudaStream_t st);
 

@@ -67,7 +67,9 @@ def test_descriptor_validation_without_gpu(mch):
     assert lib.mch_create(ctypes.byref(d3), None, ctypes.byref(h)) == 8
     bad = mch.desc_from_workload(wl, point_batch=-1)
     assert lib.mch_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
-    ov = mch.desc_from_workload(wl, overs=1)
+    ov = mch.desc_from_workload(wl, overs=2)          # no period left in R_p (P = 4)
+    assert lib.mch_create(ctypes.byref(ov), None, ctypes.byref(h)) == 1
+    ov = mch.desc_from_workload(mi.workload("channel3d_9x9x9_L3"), overs=1)
     assert lib.mch_create(ctypes.byref(ov), None, ctypes.byref(h)) == 8
     assert not h.value
     assert lib.mch_status_name(4) == b"MCH_ERR_ORDER"

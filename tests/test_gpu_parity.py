@@ -94,6 +94,30 @@ def test_hierarchy_nearest_s1(precision):
         assert err < 1e-9, (lev + 1, err)
 
 
+@pytest.mark.parametrize("name,n_fine,macro,strides", [
+    ("channel2d_4x4_n32", 32, None, None),
+    ("channel2d_17x17_L3", 64, 5, (4, 2, 1)),
+])
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_oversampling(name, n_fine, macro, strides, precision):
+    """R_p = the central 2x2 of the 4x4 periods (o = 1): centroids and E over R_p."""
+    if macro is None:
+        wl = mi.workload(name, precision=precision, overs=1)
+    else:
+        wl = mi.small_workload(name, n_fine=n_fine, macro_n=macro, strides=strides,
+                               precision=precision, overs=1)
+    s, Eg = _run_gpu(wl, rtol=1e-11)
+    Eo = _run_oracle(wl)
+    for lev in range(wl.n_levels):
+        err = block_rel_err(Eg[lev], Eo[lev]["E"], wl.n_cont, wl.dim)
+        assert err < 1e-9, (lev + 1, err)
+    W = [np.zeros((s.num_points(l), s.R, s.R)) for l in range(1, wl.n_levels + 1)]
+    G = [np.zeros((s.num_points(l), s.n_elem(l) ** 2)) for l in range(1, wl.n_levels + 1)]
+    with pytest.raises(mch.MchError) as e:
+        s.backward(W, G)
+    assert e.value.name == "MCH_ERR_UNSUPPORTED"
+
+
 def test_host_buffers_match_device_buffers():
     """Host and device buffers give the same answer. Shared-memory reductions use atomics,
     so two runs agree to the solver tolerance rather than bit for bit."""
