@@ -28,15 +28,8 @@ import numpy as np
 from . import cell, fe
 
 
-def _check_stationary(wl):
-    # the envelope form of the level's own term holds only for R_p = Y+ (o = 0)
-    if getattr(wl, "overs", 0):
-        raise NotImplementedError("gradient with oversampling (o > 0) is not derived here")
-
-
 def forward(wl, plan, media_levels):
     """Forward pass keeping every point's solve result (Phi, Xi, beta, keep, E)."""
-    _check_stationary(wl)
     res = []
     for n, lev in enumerate(plan):
         ops = cell.LevelOps(wl, n + 1)
@@ -48,7 +41,7 @@ def forward(wl, plan, media_levels):
                 I = np.zeros((ops.gf.n_nodes, wl.n_rhs))
                 for (lv, pos, w) in lev["parents"][i]:
                     I += w * res[lv - 1][pos]["Phi"].T
-            out.append(cell.solve_point(ops, kap[i], lab[i], I))
+            out.append(cell.solve_point(ops, kap[i], lab[i], I, overs=getattr(wl, "overs", 0)))
         res.append(out)
     return res
 
@@ -61,6 +54,8 @@ def loss(fwd, weights):
 def _point_adjoint(wl, ops, kap, lab, r, W, V):
     """One point of level n (ops) in the reverse sweep: its kappa gradient per level-n element
     and, for n > 1, the seed U pushed to its parents (None at level 1)."""
+    if getattr(wl, "overs", 0):
+        return _point_adjoint_region(wl, ops, kap, lab, r, W, V)
     d, R = wl.dim, wl.n_rhs
     vol = wl.rve_len ** d
     Kh, _ = fe.unit_element_matrices(d)
@@ -98,6 +93,57 @@ def _point_adjoint(wl, ops, kap, lab, r, W, V):
     return g, U
 
 
+def _point_adjoint_region(wl, ops, kap, lab, r, W, V):
+    """The same step when E is integrated over R_p, the central (P - 2o)^d periods
+    (oversampling). E_R = Phi^T A_{1,R} Phi / |R_p| is no longer stationary in Phi (the cell
+    problem minimises the energy over the whole RVE), so the level's own term enters as an
+    adjoint source instead of through the envelope form:
+        V_tot,r = V_r + sum_s What_rs A_{1,R} Phi_s,   What = (W + W^T) / |R_p|
+        A_n mu_r + C_n^T nu_r = P^T V_tot,r,   C_n mu_r = 0
+        dL/dkappa_E = sum_{e in E} [ [e in R_p] sum_rs W_rs Phi_r|e^T Khat Phi_s|e / |R_p|
+                                     - sum_r (P mu_r)|e^T Khat Phi_r|e ]
+        U_r = V_tot,r - A_1 P mu_r - C_1^T nu_r.
+    With R_p = Y+ this reduces to the envelope form of _point_adjoint."""
+    d, R = wl.dim, wl.n_rhs
+    Kh, _ = fe.unit_element_matrices(d)
+    gf, P = ops.gf, ops.P
+    reg = gf.region_mask(wl.periods, wl.overs)
+    vol = reg.sum() * gf.h ** d
+    What = (W + W.T) / vol
+    kf = cell.prolong_medium(kap, d, ops.n_c, ops.rho)
+    lf = cell.prolong_medium(lab, d, ops.n_c, ops.rho)
+    A1 = fe.stiffness_full(gf, kf)
+    AR = fe.stiffness_full(gf, kf * reg)
+    C1 = fe.constraint_rows(gf, lf, wl.n_cont, wl.periods)[r["keep"]]
+    AX = (P.T @ A1 @ P).tocsr()
+    CX = (C1 @ P).tocsr()
+    Phi = r["Phi"].T                                   # [nodes, R]
+    interior = np.isin(np.arange(gf.n_nodes), gf.interior_nodes)
+    Vt = V + (AR @ Phi) @ What.T
+    Vt[~interior] = 0.0
+    f = P.T @ Vt
+    if np.any(f):
+        mu, nu_neg = cell.saddle_solve(AX, CX, f, np.zeros((CX.shape[0], R)))
+        nu = -nu_neg                                   # A mu + C^T nu = f
+    else:
+        mu = np.zeros((P.shape[1], R))
+        nu = np.zeros((CX.shape[0], R))
+    Pmu = P @ mu
+    Pe = Phi[gf.enodes]                                # [ne, 2^d, R]
+    Me = Pmu[gf.enodes]
+    KP = np.einsum("ab,ebr->ear", Kh, Pe)
+    ge = (reg * np.einsum("rs,ear,eas->e", W / vol, Pe, KP) -
+          np.einsum("ear,ear->e", Me, KP)) * gf.h ** (d - 2)
+    ec = gf.ecoord // ops.rho
+    idx = sum(ec[:, a] * ops.n_c ** a for a in range(d))
+    g = np.bincount(idx, weights=ge, minlength=ops.n_c ** d)
+    if ops.level == 1:
+        return g, None
+    U = Vt - A1 @ Pmu - C1.T @ nu
+    U[~interior] = 0.0
+    return g, U
+
+
 def backward(wl, plan, media_levels, fwd, weights):
     """dL/dkappa per level, [npts, n_n^d], for L = sum W * E."""
     R = wl.n_rhs
@@ -127,7 +173,6 @@ def backward_sampled(wl, plan, media_fn, weights):
     seeds, so the forward and reverse sweeps run over that closure alone (Algorithm 1
     restricted to it). media_fn(level, positions) -> (kappa, labels). Returns
     ({(level, position): dL/dkappa [n_n^d]}, loss)."""
-    _check_stationary(wl)
     R = wl.n_rhs
     fwd = cell.run_sampled(wl, plan, media_fn, list(weights))
     nf_nodes = fe.Grid(wl.dim, wl.n_fine, wl.rve_len).n_nodes

@@ -10,9 +10,9 @@ import mch_inputs as mi
 from oracle import adjoint, plan
 
 
-def _setup(strides, n_fine, macro, seed=7):
+def _setup(strides, n_fine, macro, seed=7, overs=0):
     wl = mi.small_workload("channel2d_17x17_L3", n_fine=n_fine, macro_n=macro,
-                           strides=strides)
+                           strides=strides, overs=overs)
     pl = plan.level_plan(wl)
     med = [mi.media(wl, l["points"], wl.n_level(k + 1)) for k, l in enumerate(pl)]
     rng = np.random.default_rng(seed)
@@ -24,10 +24,11 @@ def _loss(wl, pl, med, W):
     return adjoint.loss(adjoint.forward(wl, pl, med), W)
 
 
-@pytest.mark.parametrize("strides,n_fine,macro", [((1,), 16, 3), ((2, 1), 16, 3),
-                                                  ((4, 2, 1), 64, 5)])
-def test_euler_identity(strides, n_fine, macro):
-    wl, pl, med, W = _setup(strides, n_fine, macro)
+@pytest.mark.parametrize("strides,n_fine,macro,overs", [((1,), 16, 3, 0), ((2, 1), 16, 3, 0),
+                                                        ((4, 2, 1), 64, 5, 0),
+                                                        ((1,), 16, 3, 1), ((2, 1), 32, 3, 1)])
+def test_euler_identity(strides, n_fine, macro, overs):
+    wl, pl, med, W = _setup(strides, n_fine, macro, overs=overs)
     fwd = adjoint.forward(wl, pl, med)
     Lv = adjoint.loss(fwd, W)
     g = adjoint.backward(wl, pl, med, fwd, W)
@@ -35,10 +36,11 @@ def test_euler_identity(strides, n_fine, macro):
     assert abs(s - Lv) <= 1e-10 * abs(Lv)
 
 
-@pytest.mark.parametrize("strides,n_fine,macro", [((1,), 16, 3), ((2, 1), 16, 3),
-                                                  ((4, 2, 1), 64, 5)])
-def test_central_differences(strides, n_fine, macro):
-    wl, pl, med, W = _setup(strides, n_fine, macro)
+@pytest.mark.parametrize("strides,n_fine,macro,overs", [((1,), 16, 3, 0), ((2, 1), 16, 3, 0),
+                                                        ((4, 2, 1), 64, 5, 0),
+                                                        ((1,), 16, 3, 1), ((2, 1), 32, 3, 1)])
+def test_central_differences(strides, n_fine, macro, overs):
+    wl, pl, med, W = _setup(strides, n_fine, macro, overs=overs)
     fwd = adjoint.forward(wl, pl, med)
     g = adjoint.backward(wl, pl, med, fwd, W)
     rng = np.random.default_rng(11)
