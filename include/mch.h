@@ -69,8 +69,9 @@ typedef struct {
   int overs;                /* oversampling layers o: E is integrated over R_p, the central
                                (P - 2o)^d periods, with centroids c_mj over R_p (Sec. 2, Eqs.
                                phi_grad, Bs_defi); constraints stay on every period. 2D only
-                               (3D: MCH_ERR_UNSUPPORTED); P - 2o >= 1; mch_backward returns
-                               MCH_ERR_UNSUPPORTED for o > 0                                */
+                               (3D: MCH_ERR_UNSUPPORTED); P - 2o >= 1. E over R_p is not
+                               stationary in the cell functions, so mch_backward treats the
+                               level's own term as an adjoint source                         */
   double rve_len;           /* l: RVE side length                                           */
   int precision;            /* MCH_MIXED (FP32 PCG inside FP64 refinement) or MCH_FP64      */
   double rtol;              /* stop when sqrt(r'M^-1 r / rho_ref) < rtol for the FP64

@@ -912,10 +912,6 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
     if (!h->lv[l].solved) return set_err(h, MCH_ERR_ORDER, "every level must be solved first");
     if (!dL_dE[l] || !dL_dkappa[l]) return set_err(h, MCH_ERR_ARG, "null gradient buffer");
   }
-  if (d.overs > 0)
-    return set_err(h, MCH_ERR_UNSUPPORTED,
-                   "gradient with oversampling: the level's own coefficients are not "
-                   "stationary in its cell functions; not built");
   cudaStream_t st = h->st;
   const int nvf = nvd(d.dim, d.n_fine);
   const bool d3 = d.dim == 3;
@@ -945,7 +941,10 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
     BALLOC(h->bw_iters, munit);
     BALLOC(h->bw_sweeps, munit);
     BALLOC(h->bw_status, munit);
-    for (int l = 0; l + 1 < Lv; ++l) BALLOC(h->lv[l].V, (size_t)h->lv[l].npts * R * nvf);
+    // seeds on the level-1 grid: levels with children, and with oversampling every level
+    // (the level's own term is an adjoint source)
+    for (int l = 0; l < Lv; ++l)
+      if (l + 1 < Lv || d.overs > 0) BALLOC(h->lv[l].V, (size_t)h->lv[l].npts * R * nvf);
     for (int l = 1; l < Lv; ++l) {
       Level &L = h->lv[l];
       BALLOC(L.par_V, (size_t)L.npts * h->slots);
@@ -963,10 +962,12 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
     h->bw_ready = true;
   }
   h->h2d = h->d2h = 0;
-  for (int l = 0; l + 1 < Lv; ++l)
-    CK(cudaMemsetAsync(h->lv[l].V, 0, (size_t)h->lv[l].npts * R * nvf * sizeof(double), st),
-       "zero seeds");
-  const double inv_vol = 1.0 / (d3 ? d.rve_len * d.rve_len * d.rve_len : d.rve_len * d.rve_len);
+  for (int l = 0; l < Lv; ++l)
+    if (h->lv[l].V)
+      CK(cudaMemsetAsync(h->lv[l].V, 0, (size_t)h->lv[l].npts * R * nvf * sizeof(double), st),
+         "zero seeds");
+  const double rlen = d.rve_len * (double)(P - 2 * d.overs) / P;
+  const double inv_vol = 1.0 / (d3 ? rlen * rlen * rlen : rlen * rlen);
   const double hf = d.rve_len / d.n_fine;
   const bool fp64 = d.precision == MCH_FP64;
   double worst = 0.0;
@@ -976,6 +977,11 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
     const size_t np = L.npts;
     CK(stage(h, h->Wd, dL_dE[li], np * R * R * sizeof(double), true), "stage dL/dE");
     const bool seeds = L.V != nullptr;
+    AdjArgs aa{(int)np, R, d.n_fine, ilog2(L.rho), nvf, L.nv, nc, ilog2(d.n_fine / P), ilog2(P),
+               h->slots, inv_vol, 1.0 / rho_pow(h, L.rho), h->Wd, L.phi,
+               seeds ? h->yc : nullptr, L.lam, seeds ? h->lamadj : nullptr, L.kappa, L.labels,
+               L.V, h->psi1, h->psi2, h->dk, L.par_V, L.par_w, h->ffs ? 1 : 0, d.overs};
+    if (d.overs > 0) CK(launch_adj_own2d(aa, st), "adjoint own term");
     if (seeds) {
       // adjoint constrained solve with right-hand side P^T V and zero targets
       if (L.rho > 1) {
@@ -1007,10 +1013,6 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
         CK(launch_level2d<float>(la, st), "adjoint fp32");
       }
     }
-    AdjArgs aa{(int)np, R, d.n_fine, ilog2(L.rho), nvf, L.nv, nc, ilog2(d.n_fine / P), ilog2(P),
-               h->slots, inv_vol, 1.0 / rho_pow(h, L.rho), h->Wd, L.phi,
-               seeds ? h->yc : nullptr, L.lam, seeds ? h->lamadj : nullptr, L.kappa, L.labels,
-               L.V, h->psi1, h->psi2, h->dk, L.par_V, L.par_w, h->ffs ? 1 : 0};
     if (d3) {
       CK(launch_adj_combine3d(aa, st), "adjoint combine");
       CK(launch_adj_grad3d(aa, hf, st), "adjoint gradient");

@@ -51,8 +51,9 @@ __global__ void k_adj_combine2d(AdjArgs a) {
 #pragma unroll
   for (int s = 0; s < R; ++s) {
     double x = 0.0;
+    if (!a.overs)
 #pragma unroll
-    for (int r = 0; r < R; ++r) x += wh[r * R + s] * phi[r];
+      for (int r = 0; r < R; ++r) x += wh[r * R + s] * phi[r];
     double pm = 0.0;
     if (a.mu) {
       const double *m = a.mu + ((size_t)pt * R + s) * a.nvc + c0;
@@ -74,6 +75,39 @@ __global__ void k_adj_grad2d(AdjArgs a) {
   if (E >= ncg * ncg) return;
   const int Ex = E % ncg, Ey = E / ncg;
   double g = 0.0;
+  if (a.overs) {
+    // direct term sum_rs W_rs Phi_r^T Khat Phi_s / |R_p| on elements inside R_p (R_p is a
+    // union of level-n elements: test one fine element's period)
+    const int P = 1 << a.lgP, o = a.overs;
+    const int px = (Ex * rho) >> a.lgmf, py = (Ey * rho) >> a.lgmf;
+    if (px >= o && px < P - o && py >= o && py < P - o) {
+      const double *Wp = a.W + (size_t)pt * R * R;
+      for (int j = 0; j < rho; ++j)
+        for (int i = 0; i < rho; ++i) {
+          const int k = (Ex * rho + i) + Wf * (Ey * rho + j);
+          double p0[R], p1[R], p2[R], p3[R];
+#pragma unroll
+          for (int s = 0; s < R; ++s) {
+            const size_t v = (size_t)pt * R + s;
+            p0[s] = phi_at(a, v, k);
+            p1[s] = phi_at(a, v, k + 1);
+            p2[s] = phi_at(a, v, k + Wf);
+            p3[s] = phi_at(a, v, k + Wf + 1);
+          }
+#pragma unroll
+          for (int s = 0; s < R; ++s) {
+            const double k0 = (4 * p0[s] - p1[s] - p2[s] - 2 * p3[s]) * (1.0 / 6.0);
+            const double k1 = (4 * p1[s] - p0[s] - p3[s] - 2 * p2[s]) * (1.0 / 6.0);
+            const double k2 = (4 * p2[s] - p0[s] - p3[s] - 2 * p1[s]) * (1.0 / 6.0);
+            const double k3 = (4 * p3[s] - p1[s] - p2[s] - 2 * p0[s]) * (1.0 / 6.0);
+#pragma unroll
+            for (int r = 0; r < R; ++r)
+              g += Wp[r * R + s] * a.inv_vol *
+                   (p0[r] * k0 + p1[r] * k1 + p2[r] * k2 + p3[r] * k3);
+          }
+        }
+    }
+  }
   for (int j = 0; j < rho; ++j)
     for (int i = 0; i < rho; ++i) {
       const int k = (Ex * rho + i) + Wf * (Ey * rho + j);
@@ -105,8 +139,9 @@ __global__ void k_adj_seed2d(AdjArgs a) {
   for (int b = threadIdx.x; b < nc; b += blockDim.x) {
     double sgm = 0.0;
     const double *Wp = a.W + (size_t)pt * R * R;
-    for (int s = 0; s < R; ++s)
-      sgm += (Wp[r * R + s] + Wp[s * R + r]) * a.inv_vol * a.lam[((size_t)pt * R + s) * nc + b];
+    if (!a.overs)
+      for (int s = 0; s < R; ++s)
+        sgm += (Wp[r * R + s] + Wp[s * R + r]) * a.inv_vol * a.lam[((size_t)pt * R + s) * nc + b];
     if (a.lamadj) sgm -= a.lamadj[((size_t)pt * R + r) * nc + b];
     sig[b] = sgm * a.inv_rho2;
   }
@@ -134,7 +169,58 @@ __global__ void k_adj_seed2d(AdjArgs a) {
   }
 }
 
+// Oversampling: V_r += sum_s What_rs A_{1,R} Phi_s at the interior fine nodes, with kappa
+// zero on the fine elements outside R_p.
+template <int R>
+__global__ void k_adj_own2d(AdjArgs a) {
+  const int pt = blockIdx.y;
+  const int nf = a.nf, Wf = nf + 1, lgr = a.lgr, ncg = nf >> lgr;
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= Wf * Wf) return;
+  const int fx = k % Wf, fy = k / Wf;
+  if (fx == 0 || fy == 0 || fx == nf || fy == nf) return;
+  const int P = 1 << a.lgP, o = a.overs;
+  const double *kc = a.kappa_c + (size_t)pt * ncg * ncg;
+  auto K = [&](int ex, int ey) {
+    const int px = ex >> a.lgmf, py = ey >> a.lgmf;
+    const bool in = px >= o && px < P - o && py >= o && py < P - o;
+    return in ? kc[(ex >> lgr) + ncg * (ey >> lgr)] : 0.0;
+  };
+  const double kSW = K(fx - 1, fy - 1), kSE = K(fx, fy - 1), kNW = K(fx - 1, fy), kNE = K(fx, fy);
+  double y[R];
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    const size_t v = (size_t)pt * R + s;
+    y[s] = q1_apply(kSW, kSE, kNW, kNE, phi_at(a, v, k - Wf - 1), phi_at(a, v, k - Wf),
+                    phi_at(a, v, k - Wf + 1), phi_at(a, v, k - 1), phi_at(a, v, k),
+                    phi_at(a, v, k + 1), phi_at(a, v, k + Wf - 1), phi_at(a, v, k + Wf),
+                    phi_at(a, v, k + Wf + 1));
+  }
+  const double *Wp = a.W + (size_t)pt * R * R;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    double u = 0.0;
+#pragma unroll
+    for (int s = 0; s < R; ++s) u += (Wp[r * R + s] + Wp[s * R + r]) * a.inv_vol * y[s];
+    double *V = const_cast<double *>(a.V);
+    V[((size_t)pt * R + r) * a.nvf + k] += u;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_adj_own2d(const AdjArgs &a, cudaStream_t st) {
+  const int Wf = a.nf + 1;
+  dim3 grid((Wf * Wf + 127) / 128, a.npts);
+  switch (a.R) {
+    case 3: k_adj_own2d<3><<<grid, 128, 0, st>>>(a); break;
+    case 6: k_adj_own2d<6><<<grid, 128, 0, st>>>(a); break;
+    case 9: k_adj_own2d<9><<<grid, 128, 0, st>>>(a); break;
+    case 12: k_adj_own2d<12><<<grid, 128, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_adj_combine2d(const AdjArgs &a, cudaStream_t st) {
   const int Wf = a.nf + 1;

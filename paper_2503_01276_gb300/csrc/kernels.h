@@ -187,10 +187,14 @@ struct AdjArgs {
   double *const *par_V;     // [pt][slots] parents' seed blocks
   const double *par_w;      // [pt][slots]
   int ffs;                  // phi stored as float-float planes
+  int overs;                // > 0: E over R_p (central (P - 2 overs)^2 periods); the own term
+                            // is an adjoint source (k_adj_own2d), no envelope terms
 };
 cudaError_t launch_adj_combine2d(const AdjArgs &a, cudaStream_t st);
 cudaError_t launch_adj_grad2d(const AdjArgs &a, cudaStream_t st);
 cudaError_t launch_adj_seed2d(const AdjArgs &a, cudaStream_t st);
+// V[pt][r] += sum_s What_rs A_{1,R} Phi_s on the level-1 grid (oversampling only).
+cudaError_t launch_adj_own2d(const AdjArgs &a, cudaStream_t st);
 cudaError_t launch_adj_combine3d(const AdjArgs &a, cudaStream_t st);
 cudaError_t launch_adj_grad3d(const AdjArgs &a, double hf, cudaStream_t st);
 cudaError_t launch_adj_seed3d(const AdjArgs &a, double hf, cudaStream_t st);

@@ -107,3 +107,25 @@ def test_autograd_directional_derivative():
     fd = (vals[0] - vals[1]) / (2 * h)
     ad = float(sum((k.grad * dv).sum() for k, dv in zip(kap, dirs)))
     assert abs(fd - ad) <= 1e-5 * abs(ad)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+@pytest.mark.parametrize("strides,n_fine,macro", [((1,), 32, 3), ((2, 1), 32, 3)])
+def test_gradient_with_oversampling(strides, n_fine, macro, precision):
+    """E over R_p (o = 1): the level's own term is an adjoint source; oracle gradient and the
+    Euler identity."""
+    wl = mi.small_workload("channel2d_17x17_L3", n_fine=n_fine, macro_n=macro, strides=strides,
+                           precision=precision, overs=1)
+    pl = plan.level_plan(wl)
+    med = [mi.media(wl, l["points"], wl.n_level(k + 1)) for k, l in enumerate(pl)]
+    rng = np.random.default_rng(7)
+    W = [rng.standard_normal((len(l["points"]), wl.n_rhs, wl.n_rhs)) for l in pl]
+    Es, g = _gpu_grad(wl, med, W)
+    loss = sum(float(np.sum(w * e)) for w, e in zip(W, Es))
+    euler = sum(float(np.sum(m[0] * gg)) for m, gg in zip(med, g))
+    assert abs(euler - loss) <= 1e-8 * abs(loss)
+    fwd = adjoint.forward(wl, pl, med)
+    ref = adjoint.backward(wl, pl, med, fwd, W)
+    for lev in range(wl.n_levels):
+        err = np.abs(g[lev] - ref[lev]).max() / np.abs(ref[lev]).max()
+        assert err < 1e-8, (lev + 1, err)

@@ -111,11 +111,6 @@ def test_oversampling(name, n_fine, macro, strides, precision):
     for lev in range(wl.n_levels):
         err = block_rel_err(Eg[lev], Eo[lev]["E"], wl.n_cont, wl.dim)
         assert err < 1e-9, (lev + 1, err)
-    W = [np.zeros((s.num_points(l), s.R, s.R)) for l in range(1, wl.n_levels + 1)]
-    G = [np.zeros((s.num_points(l), s.n_elem(l) ** 2)) for l in range(1, wl.n_levels + 1)]
-    with pytest.raises(mch.MchError) as e:
-        s.backward(W, G)
-    assert e.value.name == "MCH_ERR_UNSUPPORTED"
 
 
 def test_host_buffers_match_device_buffers():
