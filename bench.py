@@ -344,8 +344,13 @@ def main():
         tiles.append(v)
 
     def step(device_inputs=True):
+        med = med_dev if device_inputs else med_host
+        # constraint data of every level on the library's side stream, so that the later
+        # levels' setup overlaps the level-1 solve
         for lev in range(1, L + 1):
-            k, lb = (med_dev if device_inputs else med_host)[lev - 1]
+            s.prepare_level(lev, *med[lev - 1])
+        for lev in range(1, L + 1):
+            k, lb = med[lev - 1]
             s.solve_level(lev, k, lb)
             s.effective_coeffs(lev, E_dev[lev - 1] if device_inputs else E_host[lev - 1])
 

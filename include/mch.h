@@ -179,6 +179,15 @@ mch_status mch_set_timing(mch_handle *h, int enable);
 /* Statistics of the last mch_solve_level call on `level` (host struct). */
 mch_status mch_level_stats_get(const mch_handle *h, int level, mch_level_stats *out);
 
+/* Optional, ahead of mch_solve_level: stages the level's kappa and labels and computes its
+ * constraint data (setup) on a side stream of the handle, ordered after the work already
+ * enqueued on the handle's stream. A later mch_solve_level on the same level with the same
+ * kappa and labels pointers waits for that work instead of redoing it, so the setup of later
+ * levels can run while an earlier level is being solved. The buffers must not change in
+ * between. Not thread-safe with other calls on the same handle. */
+mch_status mch_prepare_level(mch_handle *h, int level, const double *kappa,
+                             const uint8_t *labels);
+
 /* Launch shape of the 2D mixed-precision level solve (no counterpart in the paper; a GPU
  * tuning parameter). Shape 0 is the default; `count` shapes exist for the level's grid, and
  * a shape is valid when its rows per thread divide the sub-block size n / P. Results do not

@@ -56,6 +56,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "mch_plan_level": (C.c_int, [C.POINTER(MchDesc), C.c_int, C.POINTER(C.c_int), P, P, P, P]),
         "mch_level_num_points": (C.c_int, [P, C.c_int]),
         "mch_set_level_variant": (C.c_int, [P, C.c_int, C.c_int]),
+        "mch_prepare_level": (C.c_int, [P, C.c_int, P, P]),
         "mch_get_level_variant": (C.c_int, [P, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "mch_autotune_level": (C.c_int, [P, C.c_int, P, P, C.POINTER(C.c_int),
                                          C.POINTER(C.c_double)]),
@@ -209,6 +210,12 @@ class Solver:
             return st
         self._check(st, "mch_solve_level")
         return st
+
+    def prepare_level(self, level: int, kappa, labels):
+        """Stages inputs and computes the constraint data of a level on the side stream
+        (mch_prepare_level); a later solve_level with the same tensors reuses it."""
+        self._check(_LIB.mch_prepare_level(self._h, level, _ptr(kappa), _ptr(labels)),
+                    "mch_prepare_level")
 
     def set_variant(self, level: int, variant: int):
         """Launch shape of the level's 2D mixed-precision solve (0 = default)."""

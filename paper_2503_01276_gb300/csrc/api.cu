@@ -45,6 +45,13 @@ struct Level {
   double *V = nullptr;            // [pt][R][nvf] backward seeds (levels with children)
   double **par_V = nullptr;       // [pt][slots] parents' seed blocks (levels > 1)
   bool solved = false;
+  // mch_prepare_level: staged inputs and constraint data computed on the side stream
+  bool prepared = false;
+  const double *prep_kappa = nullptr;
+  const uint8_t *prep_labels = nullptr;
+  cudaEvent_t prep_ev = nullptr;
+  int prep_launches = 0;
+  long long prep_h2d = 0;
   int variant = 0;                // launch shape of the 2D mixed level solve
   mch_level_stats stats{};
 };
@@ -55,6 +62,8 @@ struct mch_handle {
   mch_desc d{};
   std::vector<int> strides;
   cudaStream_t st = nullptr;
+  cudaStream_t st2 = nullptr;     // side stream of mch_prepare_level
+  cudaEvent_t ev_main = nullptr;
   int R = 0, nc = 0, nq = 0, slots = 0;
   std::vector<Level> lv;
   // scratch shared by the levels (solved one after another)
@@ -125,12 +134,13 @@ bool is_device_ptr(const void *p) {
 
 // Copies `bytes` between caller memory and library device memory in the given direction,
 // counting host traffic.
-cudaError_t stage(mch_handle *h, void *dst, const void *src, size_t bytes, bool to_device) {
+cudaError_t stage(mch_handle *h, void *dst, const void *src, size_t bytes, bool to_device,
+                  cudaStream_t on = nullptr) {
   if (to_device) {
     const bool dev = is_device_ptr(src);
     if (!dev) h->h2d += (long long)bytes;
     return cudaMemcpyAsync(dst, src, bytes, dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                           h->st);
+                           on ? on : h->st);
   }
   const bool dev = is_device_ptr(dst);
   if (!dev) h->d2h += (long long)bytes;
@@ -323,6 +333,22 @@ cudaError_t restore_phi(mch_handle *h) {
   return cudaStreamSynchronize(h->st);
 }
 
+// Stages the level's kappa and labels and computes its constraint data on stream `on`;
+// returns the number of kernels launched through *nl.
+cudaError_t setup_level(mch_handle *h, Level &L, const double *kappa, const uint8_t *labels,
+                        cudaStream_t on, int *nl) {
+  const mch_desc &d = h->d;
+  const size_t np = L.npts, ne = elems(d.dim, L.n);
+  cudaError_t e = stage(h, L.kappa, kappa, np * ne * sizeof(double), true, on);
+  if (e == cudaSuccess) e = stage(h, L.labels, labels, np * ne, true, on);
+  if (e != cudaSuccess) return e;
+  SetupArgs sa{(int)np, L.n, d.periods, d.n_cont, h->R, h->nc, d.rve_len / L.n, d.rve_len,
+               L.kappa, L.labels, L.G, L.Sinv64, L.Sinv32, L.pstat, L.dropped, L.minv, L.nv,
+               L.Sacc, L.bacc, L.kap32, L.minv32, d.overs};
+  *nl = 2;
+  return d.dim == 3 ? launch_setup3d(sa, on) : launch_setup2d(sa, on);
+}
+
 }  // namespace
 
 extern "C" {
@@ -350,6 +376,10 @@ void mch_destroy(mch_handle *h) {
   else cudaDeviceSynchronize();
   for (void *p : h->allocs) cudaFree(p);
   for (int i = 0; i < h->n_ev; ++i) cudaEventDestroy(h->ev[i]);
+  for (Level &L : h->lv)
+    if (L.prep_ev) cudaEventDestroy(L.prep_ev);
+  if (h->ev_main) cudaEventDestroy(h->ev_main);
+  if (h->st2) cudaStreamDestroy(h->st2);
   delete h;
 }
 
@@ -572,16 +602,20 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
     tags.push_back(tag);
     return cudaEventRecord(h->ev[tags.size() - 1], st);
   };
-  CK(stage(h, L.kappa, kappa, np * ne * sizeof(double), true), "stage kappa");
-  CK(stage(h, L.labels, labels, np * ne, true), "stage labels");
-
-  // ---- constraint data
-  SetupArgs sa{(int)np, L.n, P, N, R, nc, d.rve_len / L.n, d.rve_len, L.kappa, L.labels,
-               L.G, L.Sinv64, L.Sinv32, L.pstat, L.dropped, L.minv, L.nv, L.Sacc, L.bacc,
-               L.kap32, L.minv32, d.overs};
+  // ---- staged inputs and constraint data (already done if mch_prepare_level was called
+  // with the same buffers)
   CK(mark(-1), "event");
-  CK(d3 ? launch_setup3d(sa, st) : launch_setup2d(sa, st), "setup");
-  h->launches += 2;
+  // a pending preparation writes this level's buffers on the side stream: always wait for it
+  if (L.prepared) CK(cudaStreamWaitEvent(st, L.prep_ev, 0), "wait for prepared level");
+  if (L.prepared && L.prep_kappa == kappa && L.prep_labels == labels) {
+    h->launches += L.prep_launches;
+    h->h2d += L.prep_h2d;
+  } else {
+    int nl = 0;
+    CK(setup_level(h, L, kappa, labels, st, &nl), "setup");
+    h->launches += nl;
+  }
+  L.prepared = false;
   CK(mark(0), "event");
 
   // |R_p| = the central (P - 2 overs)^d periods (the whole RVE when overs = 0)
@@ -816,6 +850,32 @@ mch_status mch_set_timing(mch_handle *h, int enable) {
     }
   }
   h->timing = enable != 0;
+  return MCH_OK;
+}
+
+mch_status mch_prepare_level(mch_handle *h, int level, const double *kappa,
+                             const uint8_t *labels) {
+  if (!valid_level(h, level) || !kappa || !labels) return set_err(h, MCH_ERR_ARG, "bad argument");
+  Level &L = h->lv[level - 1];
+  if (!h->st2) {
+    CK(cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking), "side stream");
+    CK(cudaEventCreateWithFlags(&h->ev_main, cudaEventDisableTiming), "event");
+  }
+  if (!L.prep_ev) CK(cudaEventCreateWithFlags(&L.prep_ev, cudaEventDisableTiming), "event");
+  // after everything already enqueued on the handle's stream (the caller's inputs, and the
+  // previous use of this level's buffers)
+  CK(cudaEventRecord(h->ev_main, h->st), "event");
+  CK(cudaStreamWaitEvent(h->st2, h->ev_main, 0), "wait");
+  const long long h2d0 = h->h2d;
+  int nl = 0;
+  CK(setup_level(h, L, kappa, labels, h->st2, &nl), "prepare setup");
+  CK(cudaEventRecord(L.prep_ev, h->st2), "event");
+  L.prep_h2d = h->h2d - h2d0;
+  h->h2d = h2d0;
+  L.prep_launches = nl;
+  L.prep_kappa = kappa;
+  L.prep_labels = labels;
+  L.prepared = true;
   return MCH_OK;
 }
 

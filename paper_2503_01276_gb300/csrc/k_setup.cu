@@ -14,7 +14,7 @@
 //
 // Two kernels: k_setup_nodes runs on (point, slice of node rows) and writes M^-1 and adds
 // its part of S and of the per-(continuum, sub-block) element counts and centroid sums to
-// zero-initialised accumulators; k_setup_point (one CTA per point) forms the targets and
+// zero-initialised accumulators; k_setup_point (one warp per point) forms the targets and
 // the inverse. M^-1 is an FP32 reciprocal refined by two FP64 Newton steps (a preconditioner
 // only needs a fixed positive diagonal; S and every later use read the same stored value).
 #include "common.cuh"
@@ -25,7 +25,6 @@ namespace mch {
 namespace {
 
 constexpr int SN_THREADS = 256;
-constexpr int SP_THREADS = 512;
 
 __device__ __forceinline__ double fast_rcp(double d) {
   double y = (double)(1.0f / (float)d);
@@ -126,32 +125,35 @@ __global__ void __launch_bounds__(SN_THREADS) k_setup_nodes(SetupArgs a, int sli
     if (bs[i] != 0.0) atomicAdd(&bg[i], bs[i]);
 }
 
-__global__ void __launch_bounds__(SP_THREADS) k_setup_point(SetupArgs a) {
-  const int pt = blockIdx.x;
+// One warp per point (several points per CTA): the small dense factorisation is a chain of
+// dependent column steps, so warp-synchronous steps replace block-wide barriers.
+__global__ void k_setup_point(SetupArgs a, int ppb) {
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int pt = blockIdx.x * ppb + wib;
   const int P = a.P, N = a.N, R = a.R, nc = a.nc;
   const int nq = P * P;
-  const int tid = threadIdx.x;
-  if (a.status[pt] & 3) return;
+  if (pt >= a.npts) return;
+  if (a.status[pt] & 3) return;  // uniform over the warp
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  double *S = reinterpret_cast<double *>(smem_raw);      // [nc][nc]
-  double *Z = S + nc * nc;                                // [nc][nc]
-  double *bs = Z + nc * nc;                               // [nc][3] count, sum x, sum y
-  double *cen = bs + 3 * nc;                              // [MCH_MAX_CONT][2]
-  double *dorig = cen + 2 * MCH_MAX_CONT;                 // [nc]
-  __shared__ int flags;
-  if (tid == 0) flags = 0;
+  const size_t per = (size_t)2 * nc * nc + 4 * nc + 2 * MCH_MAX_CONT;
+  double *S = reinterpret_cast<double *>(smem_raw) + wib * per;  // [nc][nc]
+  double *Z = S + nc * nc;                                        // [nc][nc]
+  double *bs = Z + nc * nc;                                       // [nc][3] count, sum x, sum y
+  double *cen = bs + 3 * nc;                                      // [MCH_MAX_CONT][2]
+  double *dorig = cen + 2 * MCH_MAX_CONT;                         // [nc]
+  int flags = 0;
   const double *Sg = a.Sacc + (size_t)pt * nc * nc;
-  for (int i = tid; i < nc * nc; i += SP_THREADS) S[i] = Sg[i];
-  for (int i = tid; i < 3 * nc; i += SP_THREADS) bs[i] = a.bacc[(size_t)pt * nc * 3 + i];
-  __syncthreads();
+  for (int i = lane; i < nc * nc; i += 32) S[i] = Sg[i];
+  for (int i = lane; i < 3 * nc; i += 32) bs[i] = a.bacc[(size_t)pt * nc * 3 + i];
+  __syncwarp();
 
   // centroids c_mj over the integration region R_p (the central (P - 2 overs)^2 periods;
   // the whole RVE when the continuum is absent there, or when overs = 0)
-  if (tid < N) {
+  if (lane < N) {
     double c = 0, x = 0, y = 0, ca = 0, xa = 0, ya = 0;
     for (int q = 0; q < nq; ++q) {
-      const int b = tid * nq + q;
+      const int b = lane * nq + q;
       const int qx = q % P, qy = q / P;
       ca += bs[3 * b];
       xa += bs[3 * b + 1];
@@ -162,20 +164,20 @@ __global__ void __launch_bounds__(SP_THREADS) k_setup_point(SetupArgs a) {
         y += bs[3 * b + 2];
       }
     }
-    if (ca == 0.0) atomicOr(&flags, 8);
+    if (ca == 0.0) flags |= 8;
     if (c == 0.0) {
       c = ca;
       x = xa;
       y = ya;
     }
-    cen[2 * tid] = c > 0 ? x / c : 0.0;
-    cen[2 * tid + 1] = c > 0 ? y / c : 0.0;
+    cen[2 * lane] = c > 0 ? x / c : 0.0;
+    cen[2 * lane + 1] = c > 0 ? y / c : 0.0;
   }
-  __syncthreads();
+  __syncwarp();
 
   // scaled targets G[b][r]
   double *G = a.G + (size_t)pt * nc * R;
-  for (int t = tid; t < nc * R; t += SP_THREADS) {
+  for (int t = lane; t < nc * R; t += 32) {
     const int b = t / R, r = t % R;
     const int j = b / nq;
     double v = 0.0;
@@ -187,15 +189,15 @@ __global__ void __launch_bounds__(SP_THREADS) k_setup_point(SetupArgs a) {
     }
     G[t] = v;
   }
-  if (tid < nc) {
-    if (bs[3 * tid] == 0.0) S[tid * nc + tid] = 1.0;
-    dorig[tid] = S[tid * nc + tid];
+  for (int i = lane; i < nc; i += 32) {
+    if (bs[3 * i] == 0.0) S[i * nc + i] = 1.0;
+    dorig[i] = S[i * nc + i];
   }
-  __syncthreads();
+  __syncwarp();
 
   // Cholesky S = L L^T in place (lower triangle)
   for (int k = 0; k < nc; ++k) {
-    if (tid == 0) {
+    if (lane == 0) {
       double v = S[k * nc + k];
       if (!(v > 1e-13 * dorig[k])) {
         flags |= 4;
@@ -203,19 +205,20 @@ __global__ void __launch_bounds__(SP_THREADS) k_setup_point(SetupArgs a) {
       }
       S[k * nc + k] = sqrt(v);
     }
-    __syncthreads();
-    for (int i = k + 1 + tid; i < nc; i += SP_THREADS) S[i * nc + k] /= S[k * nc + k];
-    __syncthreads();
+    __syncwarp();
+    const double dkk = S[k * nc + k];
+    for (int i = k + 1 + lane; i < nc; i += 32) S[i * nc + k] /= dkk;
+    __syncwarp();
     const int rem = nc - k - 1;
-    for (int t = tid; t < rem * rem; t += SP_THREADS) {
+    for (int t = lane; t < rem * rem; t += 32) {
       const int i = k + 1 + t / rem, j = k + 1 + t % rem;
       if (j <= i) S[i * nc + j] -= S[i * nc + k] * S[j * nc + k];
     }
-    __syncthreads();
+    __syncwarp();
   }
 
   // Z = L^-1 (column j by forward substitution), then S^-1 = Z^T Z
-  for (int j = tid; j < nc; j += SP_THREADS) {
+  for (int j = lane; j < nc; j += 32) {
     for (int i = 0; i < nc; ++i) {
       double v = (i == j) ? 1.0 : 0.0;
       if (i > j)
@@ -223,17 +226,18 @@ __global__ void __launch_bounds__(SP_THREADS) k_setup_point(SetupArgs a) {
       Z[i * nc + j] = (i < j) ? 0.0 : v / S[i * nc + i];
     }
   }
-  __syncthreads();
+  __syncwarp();
   double *Si64 = a.Sinv64 + (size_t)pt * nc * nc;
   float *Si32 = a.Sinv32 ? a.Sinv32 + (size_t)pt * nc * nc : nullptr;
-  for (int t = tid; t < nc * nc; t += SP_THREADS) {
+  for (int t = lane; t < nc * nc; t += 32) {
     const int i = t / nc, j = t % nc;
     double v = 0.0;
     for (int k = max(i, j); k < nc; ++k) v += Z[k * nc + i] * Z[k * nc + j];
     Si64[t] = v;
     if (Si32) Si32[t] = (float)v;
   }
-  if (tid == 0) {
+  flags = __reduce_or_sync(0xffffffffu, flags);
+  if (lane == 0) {
     int nd = 0;
     for (int b = 0; b < nc; ++b) nd += (bs[3 * b] == 0.0);
     a.dropped[pt] = nd;
@@ -254,12 +258,15 @@ cudaError_t launch_setup2d(const SetupArgs &a, cudaStream_t st) {
   k_setup_nodes<<<dim3(a.npts, slices), SN_THREADS, 0, st>>>(a, slices);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t smem = sizeof(double) * (2 * a.nc * a.nc + 4 * a.nc + 2 * MCH_MAX_CONT);
+  const size_t per = sizeof(double) * (2 * (size_t)a.nc * a.nc + 4 * a.nc + 2 * MCH_MAX_CONT);
+  int ppb = (int)((96 * 1024) / per);
+  ppb = ppb < 1 ? 1 : (ppb > 4 ? 4 : ppb);
+  const size_t smem = per * ppb;
   if (smem > 48 * 1024) {
     e = cudaFuncSetAttribute(k_setup_point, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_setup_point<<<a.npts, SP_THREADS, smem, st>>>(a);
+  k_setup_point<<<(a.npts + ppb - 1) / ppb, 32 * ppb, smem, st>>>(a, ppb);
   return cudaGetLastError();
 }
 

@@ -140,6 +140,29 @@ def test_point_batch_matches_whole_level(point_batch):
         [-(-n // point_batch) for n in np_l]
 
 
+def test_prepared_levels_match_plain_solve():
+    """mch_prepare_level for every level up front (setup on the side stream, overlapping the
+    earlier levels' solves) gives the plain solve's coefficients; a solve with other buffers
+    than the prepared ones ignores the preparation."""
+    wl = mi.small_workload("channel2d_17x17_L3", n_fine=64, macro_n=9, strides=(4, 2, 1))
+    _, ref = _run_gpu(wl, rtol=1e-11)
+    s = mch.Solver.from_workload(wl, rtol=1e-11)
+    med = []
+    for lev in range(1, wl.n_levels + 1):
+        k, l = mi.media(wl, s.level_points(lev), s.n_elem(lev))
+        med.append((torch.from_numpy(k).cuda(), torch.from_numpy(l).cuda()))
+    for lev, (k, l) in enumerate(med, start=1):
+        s.prepare_level(lev, k, l)
+    for lev, (k, l) in enumerate(med, start=1):
+        s.solve_level(lev, k, l)
+        assert block_rel_err(s.effective_coeffs(lev), ref[lev - 1], wl.n_cont, wl.dim) < 1e-10
+    # prepared with a scaled copy, solved with the original: the original is used
+    k2 = med[0][0] * 3.0
+    s.prepare_level(1, k2, med[0][1])
+    s.solve_level(1, *med[0])
+    assert block_rel_err(s.effective_coeffs(1), ref[0], wl.n_cont, wl.dim) < 1e-10
+
+
 def test_full_size_17x17_sampled():
     """The benchmark workload (17x17 points, RVE grids 128/64/32, mixed precision) solved in
     full on the GPU; sampled points of every level checked against the oracle, which
