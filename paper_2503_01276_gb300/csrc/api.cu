@@ -35,6 +35,7 @@ struct Level {
   double *G = nullptr, *gI = nullptr, *Sinv64 = nullptr, *Sacc = nullptr, *bacc = nullptr;
   float *Sinv32 = nullptr;
   float *kap32 = nullptr, *minv32 = nullptr;  // 3D mixed precision: FP32 copies
+  double *kapff = nullptr;   // 2D mixed, levels > 1: float-float planes of kappa
   double *x = nullptr, *b = nullptr, *minv = nullptr;
   double *ratio = nullptr;
   int *iters = nullptr, *sweeps = nullptr, *ustat = nullptr, *pstat = nullptr, *dropped = nullptr;
@@ -187,7 +188,7 @@ cudaError_t launch_child(mch_handle *h, Level &L, double *g, int *nl = nullptr) 
   const mch_desc &d = h->d;
   ChildArgs ca{L.npts, h->R, d.n_fine, ilog2(L.rho), L.nvf, h->slots, ilog2(d.n_fine / d.periods),
                ilog2(d.periods), d.n_cont, h->nc, L.par_ptr, L.par_w, L.kappa, L.labels, L.phi,
-               h->yfine, g, 1.0 / rho_pow(h, L.rho), h->yfineR, d.overs};
+               h->yfine, g, 1.0 / rho_pow(h, L.rho), h->yfineR, d.overs, L.kapff};
   if (d.dim == 2) {
     if (nl) *nl = 1;
     return launch_child_fine2d(ca, h->ffs, h->st);
@@ -474,6 +475,7 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
       ALLOC(L.kap32, np * ne);
       ALLOC(L.minv32, np * L.nv);
     }
+    if (d.dim == 2 && d.precision == MCH_MIXED && l > 0) ALLOC(L.kapff, np * ne);
     ALLOC(L.x, np * R * L.nv);
     ALLOC(L.minv, np * L.nv);
     ALLOC(L.b, np * R * L.nv);
@@ -630,6 +632,10 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
        "targets copy");
     CK(cudaMemsetAsync(L.E, 0, np * R * R * sizeof(double), st), "zero E");
     int nl = 0;
+    if (L.kapff) {
+      CK(launch_to_ff((int)np, L.kappa, (int)ne, L.kapff, (int)ne, (int)ne, st), "kappa ff");
+      ++h->launches;
+    }
     CK(launch_child(h, L, L.gI, &nl), "child fine");
     CK(launch_gram((int)np, R, L.nvf, L.phi, ovs ? h->yfineR : h->yfine, inv_vol, L.E, st,
                    h->ffs),

@@ -18,6 +18,8 @@
 // Every kernel is a template over the storage of the level-1-grid vectors: FP64 (the FP64
 // mode) or float-float planes (ff.cuh; the mixed mode), whose arithmetic runs on the FP32
 // pipes. Level-grid vectors (x, b), kappa, the targets and E stay FP64.
+#include <type_traits>
+
 #include "common.cuh"
 #include "ff.cuh"
 #include "kernels.h"
@@ -96,6 +98,13 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
 
   const double *kc = a.kappa_c + (size_t)pt * ncg * ncg;
   const V sixth = S::from(1.0 / 6.0);
+  // kappa of a level-n element in V (prepared planes avoid a conversion per node)
+  auto kval = [&](int e) -> V {
+    if constexpr (std::is_same<V, ff>::value) {
+      if (a.kappa_ff) return ff_load(a.kappa_ff, pt, ncg * ncg, e);
+    }
+    return S::from(kc[e]);
+  };
   for (int t = tid; t < (row_hi - row_lo) * W; t += CF_THREADS) {
     const int row = row_lo + t / W, col = t % W;
     const int k = col + W * row;
@@ -105,8 +114,8 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
     if (row > 0 && row < nf && col > 0 && col < nf) {
       const int e0x = (col - 1) >> lgr, e1x = col >> lgr;
       const int e0y = (row - 1) >> lgr, e1y = row >> lgr;
-      const V kSW = S::from(kc[e0x + ncg * e0y]), kSE = S::from(kc[e1x + ncg * e0y]);
-      const V kNW = S::from(kc[e0x + ncg * e1y]), kNE = S::from(kc[e1x + ncg * e1y]);
+      const V kSW = kval(e0x + ncg * e0y), kSE = kval(e1x + ncg * e0y);
+      const V kNW = kval(e0x + ncg * e1y), kNE = kval(e1x + ncg * e1y);
       v = q1v<V>(kSW, kSE, kNW, kNE, tr[-W - 1], tr[-W], tr[-W + 1], tr[-1], tr[0], tr[1],
                  tr[W - 1], tr[W], tr[W + 1], sixth);
       if (a.yR) {

@@ -18,9 +18,10 @@ struct Shape {
 // index 0 of each n is the default shape of k_level_f32.cu
 constexpr Shape kShapes[] = {
     {16, 0, 16, 1, 1, 4}, {16, 1, 8, 2, 1, 6}, {16, 2, 4, 4, 1, 8},
-    {32, 0, 8, 4, 1, 3},  {32, 1, 4, 8, 1, 5}, {32, 2, 16, 2, 1, 2},
+    {32, 0, 8, 4, 1, 3},  {32, 1, 4, 8, 1, 5}, {32, 2, 16, 2, 1, 2}, {32, 3, 4, 4, 2, 6},
     {64, 0, 8, 8, 1, 1},  {64, 1, 4, 16, 1, 2}, {64, 2, 4, 8, 2, 2}, {64, 3, 8, 4, 2, 1},
-    {128, 0, 4, 16, 2, 1}, {128, 1, 4, 8, 4, 1},
+    {64, 4, 2, 8, 4, 4},  {64, 5, 4, 4, 4, 3},
+    {128, 0, 4, 16, 2, 1}, {128, 1, 4, 8, 4, 1}, {128, 2, 2, 8, 8, 3}, {128, 3, 4, 4, 8, 2},
     {256, 0, 2, 16, 8, 1},
 };
 
@@ -55,7 +56,12 @@ cudaError_t launch_level2d_alt(const LevelArgs<float> &a, cudaStream_t st) {
     case 64 * 16 + 1: return launch_level_nc<float, 64, 4, 16, 1, 2>(a, st);
     case 64 * 16 + 2: return launch_level_nc<float, 64, 4, 8, 2, 2>(a, st);
     case 64 * 16 + 3: return launch_level_nc<float, 64, 8, 4, 2, 1>(a, st);
+    case 32 * 16 + 3: return launch_level_nc<float, 32, 4, 4, 2, 6>(a, st);
+    case 64 * 16 + 4: return launch_level_nc<float, 64, 2, 8, 4, 4>(a, st);
+    case 64 * 16 + 5: return launch_level_nc<float, 64, 4, 4, 4, 3>(a, st);
     case 128 * 16 + 1: return launch_level_nc<float, 128, 4, 8, 4, 1>(a, st);
+    case 128 * 16 + 2: return launch_level_nc<float, 128, 2, 8, 8, 3>(a, st);
+    case 128 * 16 + 3: return launch_level_nc<float, 128, 4, 4, 8, 2>(a, st);
   }
   return cudaErrorInvalidValue;
 }

@@ -114,6 +114,7 @@ struct ChildArgs {
   double s;                       // rho^-2
   double *yR;                     // 2D oversampling: A_1 I with kappa zero outside R_p, or null
   int overs;
+  const double *kappa_ff;         // float-float planes of kappa_c (float-float storage), or null
 };
 cudaError_t launch_child_fine2d(const ChildArgs &a, bool ffs, cudaStream_t st);
 
