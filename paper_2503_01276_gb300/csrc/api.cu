@@ -194,16 +194,17 @@ cudaError_t launch_child(mch_handle *h, Level &L, double *g, int *nl = nullptr) 
     return launch_child_fine2d(ca, h->ffs, h->st);
   }
   if (nl) *nl = 2;
-  cudaError_t e = launch_interp3d(ca, h->st);
+  cudaError_t e = launch_interp3d(ca, h->st, h->ffs);
   if (e != cudaSuccess) return e;
-  return launch_fine_apply3d(ca, d.rve_len / d.n_fine, h->st);
+  return launch_fine_apply3d(ca, d.rve_len / d.n_fine, h->st, h->ffs);
 }
 
 cudaError_t launch_prolong(mch_handle *h, Level &L) {
   if (h->d.dim == 2)
     return launch_prolong_add2d(L.npts, h->R, h->d.n_fine, L.rho, L.x, L.nv, L.phi, L.nvf, h->st,
                                 h->ffs);
-  return launch_prolong_add3d(L.npts, h->R, h->d.n_fine, L.rho, L.x, L.nv, L.phi, L.nvf, h->st);
+  return launch_prolong_add3d(L.npts, h->R, h->d.n_fine, L.rho, L.x, L.nv, L.phi, L.nvf, h->st,
+                              h->ffs);
 }
 
 // yf is a level-1-grid vector in the handle's storage (ffs) or, for the backward seeds, FP64
@@ -212,7 +213,8 @@ cudaError_t launch_restrict(mch_handle *h, Level &L, const double *yf, double sc
   if (h->d.dim == 2)
     return launch_restrict2d(L.npts, h->R, h->d.n_fine, L.rho, yf, L.nvf, scale, out, L.nv, h->st,
                              ffs);
-  return launch_restrict3d(L.npts, h->R, h->d.n_fine, L.rho, yf, L.nvf, scale, out, L.nv, h->st);
+  return launch_restrict3d(L.npts, h->R, h->d.n_fine, L.rho, yf, L.nvf, scale, out, L.nv, h->st,
+                           ffs);
 }
 
 // grows the 3D level-solve scratch to `units_nv` node entries per vector and `acc` doubles
@@ -414,7 +416,7 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
   h->R = d.n_cont * (1 + d.dim);
   h->nq = nq;
   h->nc = nc;
-  h->ffs = d.dim == 2 && d.precision == MCH_MIXED;
+  h->ffs = d.precision == MCH_MIXED;
   h->slots = 1 << d.dim;
 
   std::vector<LevelPlan> plans;
@@ -475,7 +477,7 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
       ALLOC(L.kap32, np * ne);
       ALLOC(L.minv32, np * L.nv);
     }
-    if (d.dim == 2 && d.precision == MCH_MIXED && l > 0) ALLOC(L.kapff, np * ne);
+    if (d.precision == MCH_MIXED && l > 0) ALLOC(L.kapff, np * ne);
     ALLOC(L.x, np * R * L.nv);
     ALLOC(L.minv, np * L.nv);
     ALLOC(L.b, np * R * L.nv);

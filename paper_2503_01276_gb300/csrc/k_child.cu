@@ -28,31 +28,6 @@ namespace mch {
 
 namespace {
 
-struct F64S {
-  using V = double;
-  __device__ static V ld(const double *b, size_t v, int nv, int k) { return b[v * nv + k]; }
-  __device__ static void st(double *b, size_t v, int nv, int k, V x) { b[v * nv + k] = x; }
-  __device__ static V from(double d) { return d; }
-  __device__ static double to(V x) { return x; }
-  __device__ static V zero() { return 0.0; }
-  __device__ static V shfl_xor(V v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
-  // acc += x * y + y' * x'
-  __device__ static void acc2(V &acc, V x, V y, V x2, V y2) { acc += x * y + x2 * y2; }
-};
-
-struct FFS {
-  using V = ff;
-  __device__ static V ld(const double *b, size_t v, int nv, int k) { return ff_load(b, v, nv, k); }
-  __device__ static void st(double *b, size_t v, int nv, int k, V x) { ff_store(b, v, nv, k, x); }
-  __device__ static V from(double d) { return ff_from(d); }
-  __device__ static double to(V x) { return ff_to(x); }
-  __device__ static V zero() { return ff{0.f, 0.f}; }
-  __device__ static V shfl_xor(V v, int o) {
-    return ff{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
-  }
-  __device__ static void acc2(V &acc, V x, V y, V x2, V y2) { ff_acc(acc, x * y + x2 * y2); }
-};
-
 template <class S>
 __device__ __forceinline__ typename S::V seg_sum_s(typename S::V v, int seg) {
   for (int o = seg >> 1; o > 0; o >>= 1) v = v + S::shfl_xor(v, o);

@@ -11,6 +11,9 @@
 // - P mu_s, Psi = 1/2 sum_r What_rs Phi_r - P mu_s; dL/dkappa_E = sum_{fine e in E}
 // h_f Psi_s|e^T Khat Phi_s|e; U_r = V_r + A_1 Psi'_r + rho^-3 Ct_1^T sigma_r pushed to the
 // parents.
+#include <type_traits>
+
+#include "ff.cuh"
 #include "k3d.cuh"
 #include "kernels.h"
 
@@ -64,23 +67,53 @@ __global__ void __launch_bounds__(F3_THREADS) k_apply3d(ApplyArgs a, double h) {
   y[k] = r;
 }
 
+// The 3D stencil of k3d.cuh for any value type (FP64 or float-float): up to the factor h.
+template <typename V>
+__device__ __forceinline__ V q1_apply3d_v(const V (&v)[3][3][3], const V (&k)[2][2][2], V third,
+                                          V twelfth) {
+  const V ksum = ((k[0][0][0] + k[0][0][1]) + (k[0][1][0] + k[0][1][1])) +
+                 ((k[1][0][0] + k[1][0][1]) + (k[1][1][0] + k[1][1][1]));
+  V acc = k[0][0][0] * v[0][0][0];
+#pragma unroll
+  for (int c = 1; c < 8; ++c) {
+    const int oz = c >> 2, oy = (c >> 1) & 1, ox = c & 1;
+    acc += k[oz][oy][ox] * v[2 * oz][2 * oy][2 * ox];
+  }
+#pragma unroll
+  for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+    for (int ox = 0; ox < 2; ++ox) acc += (k[0][oy][ox] + k[1][oy][ox]) * v[1][2 * oy][2 * ox];
+#pragma unroll
+  for (int oz = 0; oz < 2; ++oz)
+#pragma unroll
+    for (int ox = 0; ox < 2; ++ox) acc += (k[oz][0][ox] + k[oz][1][ox]) * v[2 * oz][1][2 * ox];
+#pragma unroll
+  for (int oz = 0; oz < 2; ++oz)
+#pragma unroll
+    for (int oy = 0; oy < 2; ++oy) acc += (k[oz][oy][0] + k[oz][oy][1]) * v[2 * oz][2 * oy][1];
+  return ksum * v[1][1][1] * third - acc * twelfth;
+}
+
+template <class S>
 __global__ void __launch_bounds__(F3_THREADS) k_interp3d(ChildArgs a) {
+  using V = typename S::V;
   const int unit = blockIdx.y, pt = unit / a.R, r = unit % a.R;
   const int k = blockIdx.x * F3_THREADS + threadIdx.x;
   if (k >= a.nvf) return;
-  double v = 0.0;
+  V v = S::zero();
   for (int s = 0; s < a.slots; ++s) {
-    const double w = a.par_w[pt * a.slots + s];
-    if (w != 0.0) v += w * a.par_ptr[pt * a.slots + s][(size_t)r * a.nvf + k];
+    const double *pp = a.par_ptr[pt * a.slots + s];
+    if (pp) v += S::from(a.par_w[pt * a.slots + s]) * S::ld(pp, r, a.nvf, k);
   }
-  a.phi[(size_t)unit * a.nvf + k] = v;
+  S::st(a.phi, unit, a.nvf, k, v);
 }
 
 // y = h_f A_1 phi and g -= s C_1 phi: one thread per interior node column of the level-1
 // lattice, walking z with sliding windows; the constraint functionals go per (element
 // column, label) into registers, per CTA into shared memory, then into g.
-template <int NCN>
+template <int NCN, class S>
 __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double hf) {
+  using V = typename S::V;
   const int unit = blockIdx.y, pt = unit / a.R, r = unit % a.R;
   const int nf = a.nf, W = nf + 1, ni = nf - 1, lgr = a.lgr, ncg = nf >> lgr;
   const int P = 1 << a.lgP, mf = 1 << a.lgmf, nq = P * P * P;
@@ -91,37 +124,43 @@ __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double
   if (t < ni * ni) {
     const int kx = 1 + t % ni, ky = 1 + t / ni;
     const size_t W2 = (size_t)W * W;
-    const double *ph = a.phi + (size_t)unit * a.nvf;
-    double *y = a.y + (size_t)unit * a.nvf;
     const double *kc = a.kappa_c + (size_t)pt * ncg * ncg * ncg;
     const uint8_t *lc = a.labels_c + (size_t)pt * ncg * ncg * ncg;
     const size_t base = kx + (size_t)W * ky;
-    double v[3][3][3], kk[2][2][2];
+    const V third = S::from(1.0 / 3.0), twelfth = S::from(1.0 / 12.0), hv = S::from(hf);
+    auto kval = [&](size_t c) -> V {
+      if constexpr (std::is_same<V, ff>::value) {
+        if (a.kappa_ff) return ff_load(a.kappa_ff, pt, ncg * ncg * ncg, (int)c);
+      }
+      return S::from(kc[c]);
+    };
+    V v[3][3][3], kk[2][2][2];
     int lo[2][2], up[2][2];
-    auto load_v = [&](double (&pl)[3][3], int z) {
+    auto load_v = [&](V (&pl)[3][3], int z) {
 #pragma unroll
       for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-        for (int dx = 0; dx < 3; ++dx) pl[dy][dx] = ph[base + W2 * z + (dx - 1) + W * (dy - 1)];
+        for (int dx = 0; dx < 3; ++dx)
+          pl[dy][dx] = S::ld(a.phi, unit, a.nvf, (int)(base + W2 * z + (dx - 1) + W * (dy - 1)));
     };
-    auto load_k = [&](double (&pl)[2][2], int (&lp)[2][2], int ez) {
+    auto load_k = [&](V (&pl)[2][2], int (&lp)[2][2], int ez) {
 #pragma unroll
       for (int sy = 0; sy < 2; ++sy)
 #pragma unroll
         for (int sx = 0; sx < 2; ++sx) {
           const size_t c = cidx((kx - 1 + sx) >> lgr, (ky - 1 + sy) >> lgr, ez >> lgr, ncg);
-          pl[sy][sx] = kc[c];
+          pl[sy][sx] = kval(c);
           lp[sy][sx] = lc[c];
         }
     };
     load_v(v[0], 0);
     load_v(v[1], 1);
     load_k(kk[0], lo, 0);
-    double acc[4][NCN];
+    V acc[4][NCN];
 #pragma unroll
     for (int c = 0; c < 4; ++c)
 #pragma unroll
-      for (int j = 0; j < NCN; ++j) acc[c][j] = 0.0;
+      for (int j = 0; j < NCN; ++j) acc[c][j] = S::zero();
     int zb = 0;
     auto flush = [&]() {
 #pragma unroll
@@ -130,20 +169,22 @@ __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double
         const int bb = (zb * P + (ey >> a.lgmf)) * P + (ex >> a.lgmf);
 #pragma unroll
         for (int j = 0; j < NCN; ++j) {
-          if (acc[c][j] != 0.0) atomicAdd(&bins[j * nq + bb], acc[c][j]);
-          acc[c][j] = 0.0;
+          const double d = S::to(acc[c][j]);
+          if (d != 0.0) atomicAdd(&bins[j * nq + bb], d);
+          acc[c][j] = S::zero();
         }
       }
     };
     for (int kz = 1; kz < nf; ++kz) {
       load_v(v[2], kz + 1);
       load_k(kk[1], up, kz);
-      const double val = v[1][1][1];
-      y[base + W2 * kz] = hf * q1_apply3d<double>(v, kk);
+      const V val = v[1][1][1];
+      S::st(a.y, unit, a.nvf, (int)(base + W2 * kz), hv * q1_apply3d_v<V>(v, kk, third, twelfth));
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int j = 0; j < NCN; ++j) acc[c][j] += (lo[c >> 1][c & 1] == j) ? val : 0.0;
+        for (int j = 0; j < NCN; ++j)
+          if (lo[c >> 1][c & 1] == j) acc[c][j] += val;
       if ((kz & (mf - 1)) == 0) {
         flush();
         zb = kz / mf;
@@ -151,7 +192,8 @@ __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int j = 0; j < NCN; ++j) acc[c][j] += (up[c >> 1][c & 1] == j) ? val : 0.0;
+        for (int j = 0; j < NCN; ++j)
+          if (up[c >> 1][c & 1] == j) acc[c][j] += val;
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -175,10 +217,12 @@ __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double
     if (bins[i] != 0.0) atomicAdd(&g[(size_t)i * a.R], -a.s * bins[i]);
 }
 
-// out = scale P^T y on the coarse lattice (one thread per coarse lattice entry).
+// out = scale P^T y on the coarse lattice (one thread per coarse lattice entry; out FP64).
+template <class S>
 __global__ void __launch_bounds__(F3_THREADS) k_restrict3d(int nf, int lgr, const double *yf,
                                                            int nvf, double scale, double *outc,
                                                            int nvc) {
+  using V = typename S::V;
   const int unit = blockIdx.y;
   const int rho = 1 << lgr, ncg = nf >> lgr, Wc = ncg + 1, Wf = nf + 1;
   const int k = blockIdx.x * F3_THREADS + threadIdx.x;
@@ -190,51 +234,63 @@ __global__ void __launch_bounds__(F3_THREADS) k_restrict3d(int nf, int lgr, cons
     o[k] = 0.0;
     return;
   }
-  const double *y = yf + (size_t)unit * nvf;
-  const double ir = 1.0 / rho;  // exact: rho is a power of two
-  double s = 0.0;
+  const float ir = 1.0f / rho;  // exact: rho is a power of two
+  V s = S::zero();
   for (int dz = 1 - rho; dz < rho; ++dz) {
-    const double wz = 1.0 - fabs((double)dz) * ir;
-    const int fz = Kz * rho + dz;
-    double sy = 0.0;
+    const float wz = 1.0f - fabsf((float)dz) * ir;
+    V sy = S::zero();
     for (int dy = 1 - rho; dy < rho; ++dy) {
-      const double wy = 1.0 - fabs((double)dy) * ir;
-      const size_t row = (size_t)Wf * ((Kz * rho + dz) * (size_t)Wf + Ky * rho + dy);
-      double sx = 0.0;
+      const float wy = 1.0f - fabsf((float)dy) * ir;
+      const int row = Wf * ((Kz * rho + dz) * Wf + Ky * rho + dy);
+      V sx = S::zero();
       for (int dx = 1 - rho; dx < rho; ++dx)
-        sx += (1.0 - fabs((double)dx) * ir) * y[row + Kx * rho + dx];
-      sy += wy * sx;
+        sx += S::ld(yf, unit, nvf, row + Kx * rho + dx) * (1.0f - fabsf((float)dx) * ir);
+      sy += sx * wy;
     }
-    s += wz * sy;
-    (void)fz;
+    s += sy * wz;
   }
-  o[k] = scale * s;
+  o[k] = scale * S::to(s);
 }
 
-// phi += P x_c (one thread per fine lattice node).
+// phi += P x_c: one thread per coarse cell; the cell's rho^3 fine nodes (lower corners
+// included) get the trilinear interpolant of its eight coarse values (x FP64).
+template <class S>
 __global__ void __launch_bounds__(F3_THREADS) k_prolong_add3d(int nf, int lgr, const double *xc,
                                                               int nvc, double *phif, int nvf) {
+  using V = typename S::V;
   const int unit = blockIdx.y;
   const int rho = 1 << lgr, ncg = nf >> lgr, Wc = ncg + 1, Wf = nf + 1;
-  const int k = blockIdx.x * F3_THREADS + threadIdx.x;
-  if (k >= Wf * Wf * Wf) return;
-  const int fx = k % Wf, fy = (k / Wf) % Wf, fz = k / (Wf * Wf);
-  const int bx = min(fx >> lgr, ncg - 1), by = min(fy >> lgr, ncg - 1), bz = min(fz >> lgr, ncg - 1);
-  const double ir = 1.0 / rho;
-  const double tx = (fx - (bx << lgr)) * ir, ty = (fy - (by << lgr)) * ir,
-               tz = (fz - (bz << lgr)) * ir;
+  const int cell = blockIdx.x * F3_THREADS + threadIdx.x;
+  if (cell >= ncg * ncg * ncg) return;
+  const int bx = cell % ncg, by = (cell / ncg) % ncg, bz = cell / (ncg * ncg);
   const double *x = xc + (size_t)unit * nvc + bx + (size_t)Wc * (by + (size_t)Wc * bz);
   const size_t sy = Wc, sz = (size_t)Wc * Wc;
-  const double c00 = (1 - tx) * x[0] + tx * x[1];
-  const double c10 = (1 - tx) * x[sy] + tx * x[sy + 1];
-  const double c01 = (1 - tx) * x[sz] + tx * x[sz + 1];
-  const double c11 = (1 - tx) * x[sz + sy] + tx * x[sz + sy + 1];
-  const double c0 = (1 - ty) * c00 + ty * c10, c1 = (1 - ty) * c01 + ty * c11;
-  phif[(size_t)unit * nvf + k] += (1 - tz) * c0 + tz * c1;
-  (void)rho;
+  const V x000 = S::from(x[0]), x100 = S::from(x[1]), x010 = S::from(x[sy]),
+          x110 = S::from(x[sy + 1]), x001 = S::from(x[sz]), x101 = S::from(x[sz + 1]),
+          x011 = S::from(x[sz + sy]), x111 = S::from(x[sz + sy + 1]);
+  const float ir = 1.0f / rho;
+  for (int kz = 0; kz < rho; ++kz) {
+    const float tz = kz * ir;
+    for (int jy = 0; jy < rho; ++jy) {
+      const float ty = jy * ir;
+      const V a0 = x000 + (x010 - x000) * ty, a1 = x100 + (x110 - x100) * ty;
+      const V b0 = x001 + (x011 - x001) * ty, b1 = x101 + (x111 - x101) * ty;
+      const V c0 = a0 + (b0 - a0) * tz, c1 = a1 + (b1 - a1) * tz;
+      const V dc = c1 - c0;
+      const int row = (bx * rho) + Wf * ((by * rho + jy) + Wf * (bz * rho + kz));
+      for (int ix = 0; ix < rho; ++ix) {
+        const int k = row + ix;
+        S::st(phif, unit, nvf, k, S::ld(phif, unit, nvf, k) + (c0 + dc * (ix * ir)));
+      }
+    }
+  }
 }
 
 // ---- backward
+
+__device__ __forceinline__ double phi3(const AdjArgs &a, size_t v, size_t k) {
+  return a.ffs ? ff_to(ff_load(a.phi, v, a.nvf, (int)k)) : a.phi[v * a.nvf + k];
+}
 
 template <int R>
 __global__ void __launch_bounds__(F3_THREADS) k_adj_combine3d(AdjArgs a) {
@@ -251,7 +307,7 @@ __global__ void __launch_bounds__(F3_THREADS) k_adj_combine3d(AdjArgs a) {
     for (int s = 0; s < R; ++s) wh[r * R + s] = (Wp[r * R + s] + Wp[s * R + r]) * a.inv_vol;
   double phi[R];
 #pragma unroll
-  for (int r = 0; r < R; ++r) phi[r] = a.phi[((size_t)pt * R + r) * a.nvf + k];
+  for (int r = 0; r < R; ++r) phi[r] = phi3(a, (size_t)pt * R + r, k);
   const int bx = min(fx >> lgr, ncg - 1), by = min(fy >> lgr, ncg - 1), bz = min(fz >> lgr, ncg - 1);
   const double ir = 1.0 / (1 << lgr);
   const double tx = (fx - (bx << lgr)) * ir, ty = (fy - (by << lgr)) * ir,
@@ -297,7 +353,7 @@ __global__ void __launch_bounds__(F3_THREADS) k_adj_grad3d(AdjArgs a, double hf)
           double p[8], q[8];
 #pragma unroll
           for (int c = 0; c < 8; ++c) {
-            p[c] = a.phi[o + off[c]];
+            p[c] = phi3(a, (size_t)pt * R + s, k0 + off[c]);
             q[c] = a.psi2[o + off[c]];
           }
           // Khat p at corner c: 1/3 p_c - 1/12 (sum of the 3 face-diagonal corners c^3, c^5,
@@ -374,33 +430,41 @@ cudaError_t launch_apply3d(const ApplyArgs &a, double h, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_interp3d(const ChildArgs &a, cudaStream_t st) {
+cudaError_t launch_interp3d(const ChildArgs &a, cudaStream_t st, bool ffs) {
   dim3 grid((a.nvf + F3_THREADS - 1) / F3_THREADS, a.npts * a.R);
-  k_interp3d<<<grid, F3_THREADS, 0, st>>>(a);
+  if (ffs) k_interp3d<FFS><<<grid, F3_THREADS, 0, st>>>(a);
+  else k_interp3d<F64S><<<grid, F3_THREADS, 0, st>>>(a);
   return cudaGetLastError();
 }
 
-cudaError_t launch_fine_apply3d(const ChildArgs &a, double hf, cudaStream_t st) {
+cudaError_t launch_fine_apply3d(const ChildArgs &a, double hf, cudaStream_t st, bool ffs) {
   if (a.nc > MCH_MAX_NC3) return cudaErrorInvalidValue;
   const int ni = a.nf - 1;
   dim3 grid((ni * ni + F3_THREADS - 1) / F3_THREADS, a.npts * a.R);
-  if (a.N <= 2) k_fine_apply3d<2><<<grid, F3_THREADS, 0, st>>>(a, hf);
-  else k_fine_apply3d<4><<<grid, F3_THREADS, 0, st>>>(a, hf);
+  if (ffs) {
+    if (a.N <= 2) k_fine_apply3d<2, FFS><<<grid, F3_THREADS, 0, st>>>(a, hf);
+    else k_fine_apply3d<4, FFS><<<grid, F3_THREADS, 0, st>>>(a, hf);
+  } else {
+    if (a.N <= 2) k_fine_apply3d<2, F64S><<<grid, F3_THREADS, 0, st>>>(a, hf);
+    else k_fine_apply3d<4, F64S><<<grid, F3_THREADS, 0, st>>>(a, hf);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_restrict3d(int npts, int R, int nf, int rho, const double *yf, int nvf,
-                              double scale, double *outc, int nvc, cudaStream_t st) {
+                              double scale, double *outc, int nvc, cudaStream_t st, bool ffs) {
   dim3 grid((nvc + F3_THREADS - 1) / F3_THREADS, npts * R);
-  k_restrict3d<<<grid, F3_THREADS, 0, st>>>(nf, __builtin_ctz(rho), yf, nvf, scale, outc, nvc);
+  if (ffs) k_restrict3d<FFS><<<grid, F3_THREADS, 0, st>>>(nf, __builtin_ctz(rho), yf, nvf, scale, outc, nvc);
+  else k_restrict3d<F64S><<<grid, F3_THREADS, 0, st>>>(nf, __builtin_ctz(rho), yf, nvf, scale, outc, nvc);
   return cudaGetLastError();
 }
 
 cudaError_t launch_prolong_add3d(int npts, int R, int nf, int rho, const double *xc, int nvc,
-                                 double *phif, int nvf, cudaStream_t st) {
-  const int Wf = nf + 1;
-  dim3 grid((Wf * Wf * Wf + F3_THREADS - 1) / F3_THREADS, npts * R);
-  k_prolong_add3d<<<grid, F3_THREADS, 0, st>>>(nf, __builtin_ctz(rho), xc, nvc, phif, nvf);
+                                 double *phif, int nvf, cudaStream_t st, bool ffs) {
+  const int ncg = nf / rho;
+  dim3 grid((ncg * ncg * ncg + F3_THREADS - 1) / F3_THREADS, npts * R);
+  if (ffs) k_prolong_add3d<FFS><<<grid, F3_THREADS, 0, st>>>(nf, __builtin_ctz(rho), xc, nvc, phif, nvf);
+  else k_prolong_add3d<F64S><<<grid, F3_THREADS, 0, st>>>(nf, __builtin_ctz(rho), xc, nvc, phif, nvf);
   return cudaGetLastError();
 }
 

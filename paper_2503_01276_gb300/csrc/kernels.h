@@ -162,14 +162,15 @@ cudaError_t launch_level3d(const Level3Args<T> &a, cudaStream_t st);
 
 // y = A(kappa_c prolonged) x + cb * b on an n-grid, kappa on the (n / rho)-grid.
 cudaError_t launch_apply3d(const ApplyArgs &a, double h, cudaStream_t st);
+// Level-1-grid vectors in FP64 or, with ffs, float-float planes (ff.cuh).
 // phi[pt][r] = sum_t w_t Phi_t[r] on the level-1 lattice.
-cudaError_t launch_interp3d(const ChildArgs &a, cudaStream_t st);
+cudaError_t launch_interp3d(const ChildArgs &a, cudaStream_t st, bool ffs);
 // y = A_1 phi (child kappa prolonged to the level-1 grid) and g -= s * C_1 phi.
-cudaError_t launch_fine_apply3d(const ChildArgs &a, double hf, cudaStream_t st);
+cudaError_t launch_fine_apply3d(const ChildArgs &a, double hf, cudaStream_t st, bool ffs);
 cudaError_t launch_restrict3d(int npts, int R, int nf, int rho, const double *yf, int nvf,
-                              double scale, double *outc, int nvc, cudaStream_t st);
+                              double scale, double *outc, int nvc, cudaStream_t st, bool ffs);
 cudaError_t launch_prolong_add3d(int npts, int R, int nf, int rho, const double *xc, int nvc,
-                                 double *phif, int nvf, cudaStream_t st);
+                                 double *phif, int nvf, cudaStream_t st, bool ffs);
 
 // Backward pass kernels (k_adjoint.cu).
 struct AdjArgs {
