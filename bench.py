@@ -289,6 +289,9 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the unbatched per-macropoint FP64 comparator")
+    ap.add_argument("--tiles", default=None,
+                    help="comma-separated launch shapes per level instead of autotuning "
+                         "(fixed launch counts, for profiling)")
     ap.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_leg is not None:
@@ -339,9 +342,14 @@ def main():
 
     # launch shapes of the level solves, chosen by the library's autotuner on this workload
     tiles = []
-    for lev in range(1, L + 1):
-        v, ms = s.autotune_level(lev, *med_dev[lev - 1])
-        tiles.append(v)
+    if args.tiles:
+        tiles = [int(v) for v in args.tiles.split(",")]
+        for lev, v in enumerate(tiles, start=1):
+            s.set_variant(lev, v)
+    else:
+        for lev in range(1, L + 1):
+            v, ms = s.autotune_level(lev, *med_dev[lev - 1])
+            tiles.append(v)
 
     def step(device_inputs=True):
         med = med_dev if device_inputs else med_host

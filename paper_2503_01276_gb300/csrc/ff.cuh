@@ -102,6 +102,11 @@ __device__ __forceinline__ void ff_store(double *base, size_t v, int nv, int k, 
 // stores, conversions and the two reduction helpers the kernels need.
 struct F64S {
   using V = double;
+  using P = double *;
+  // base of vector v, then entry k of it with 32-bit offsets
+  __device__ static P vec(const double *b, size_t v, int nv) { return const_cast<P>(b) + v * nv; }
+  __device__ static V ldv(P p, int, int k) { return p[k]; }
+  __device__ static void stv(P p, int, int k, V x) { p[k] = x; }
   __device__ static V ld(const double *b, size_t v, int nv, int k) { return b[v * nv + k]; }
   __device__ static void st(double *b, size_t v, int nv, int k, V x) { b[v * nv + k] = x; }
   __device__ static V from(double d) { return d; }
@@ -114,6 +119,15 @@ struct F64S {
 
 struct FFS {
   using V = ff;
+  using P = float *;
+  __device__ static P vec(const double *b, size_t v, int nv) {
+    return const_cast<float *>(reinterpret_cast<const float *>(b)) + v * 2 * (size_t)nv;
+  }
+  __device__ static V ldv(P p, int nv, int k) { return ff{p[k], p[nv + k]}; }
+  __device__ static void stv(P p, int nv, int k, V x) {
+    p[k] = x.h;
+    p[nv + k] = x.l;
+  }
   __device__ static V ld(const double *b, size_t v, int nv, int k) { return ff_load(b, v, nv, k); }
   __device__ static void st(double *b, size_t v, int nv, int k, V x) { ff_store(b, v, nv, k, x); }
   __device__ static V from(double d) { return ff_from(d); }

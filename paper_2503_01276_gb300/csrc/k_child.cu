@@ -48,12 +48,13 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
   const int row_hi = min(row_lo + CF_BR, nf + 1);  // one past the last own row
   __shared__ V tile[(CF_BR + 2) * 257];
   __shared__ double bins[MCH_MAX_NC];
-  __shared__ const double *pp[4];
+  __shared__ typename S::P pp[4];
   __shared__ V pw[4];
   const int tid = threadIdx.x;
   if (tid < a.slots) {
     pw[tid] = S::from(a.par_w[pt * a.slots + tid]);
-    pp[tid] = a.par_ptr[pt * a.slots + tid];
+    const double *b = a.par_ptr[pt * a.slots + tid];
+    pp[tid] = b ? S::vec(b, r, a.nvf) : nullptr;
   }
   for (int t = tid; t < a.nc; t += CF_THREADS) bins[t] = 0.0;
   __syncthreads();
@@ -65,7 +66,7 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
     if (row >= 0 && row <= nf) {
       const int k = col + W * row;
       for (int s = 0; s < a.slots; ++s)
-        if (pp[s]) v += pw[s] * S::ld(pp[s], r, a.nvf, k);
+        if (pp[s]) v += pw[s] * S::ldv(pp[s], a.nvf, k);
     }
     tile[t] = v;
   }
@@ -73,6 +74,8 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
 
   const double *kc = a.kappa_c + (size_t)pt * ncg * ncg;
   const V sixth = S::from(1.0 / 6.0);
+  const typename S::P phv = S::vec(a.phi, unit, a.nvf), yv = S::vec(a.y, unit, a.nvf);
+  const typename S::P yrv = a.yR ? S::vec(a.yR, unit, a.nvf) : nullptr;
   // kappa of a level-n element in V (prepared planes avoid a conversion per node)
   auto kval = [&](int e) -> V {
     if constexpr (std::is_same<V, ff>::value) {
@@ -84,7 +87,7 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
     const int row = row_lo + t / W, col = t % W;
     const int k = col + W * row;
     const V *tr = tile + (row - row_lo + 1) * W + col;
-    S::st(a.phi, unit, a.nvf, k, tr[0]);
+    S::stv(phv, a.nvf, k, tr[0]);
     V v = S::zero(), vR = S::zero();
     if (row > 0 && row < nf && col > 0 && col < nf) {
       const int e0x = (col - 1) >> lgr, e1x = col >> lgr;
@@ -107,8 +110,8 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
                     tr[-W + 1], tr[-1], tr[0], tr[1], tr[W - 1], tr[W], tr[W + 1], sixth);
       }
     }
-    S::st(a.y, unit, a.nvf, k, v);
-    if (a.yR) S::st(a.yR, unit, a.nvf, k, vR);
+    S::stv(yv, a.nvf, k, v);
+    if (yrv) S::stv(yrv, a.nvf, k, vR);
   }
 
   // C_1 I on the band's element rows: element corner sums per (label, sub-block). Warp w
@@ -171,12 +174,15 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram2d(int nv, int slices, const
   V acc[NP];
 #pragma unroll
   for (int p = 0; p < NP; ++p) acc[p] = S::zero();
+  const typename S::P x0 = S::vec(X, (size_t)pt * R, nv), y0 = S::vec(Y, (size_t)pt * R, nv);
+  // vector r of the point starts r * (entries of one vector) after vector 0
+  const int vstride = (int)(S::vec(X, 1, nv) - S::vec(X, 0, nv));
   for (int k = k0 + threadIdx.x; k < k1; k += GR_THREADS) {
     V xv[R], yv[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) {
-      xv[r] = S::ld(X, (size_t)pt * R + r, nv, k);
-      yv[r] = S::ld(Y, (size_t)pt * R + r, nv, k);
+      xv[r] = S::ldv(x0 + r * vstride, nv, k);
+      yv[r] = S::ldv(y0 + r * vstride, nv, k);
     }
     int p = 0;
 #pragma unroll
@@ -220,13 +226,14 @@ __global__ void k_restrict2d(int nf, const double *yf, int nvf, double scale, do
     return;
   }
   const int c0 = (Ky * RHO) * Wf + Kx * RHO;
+  const typename S::P yb = S::vec(yf, unit, nvf);
   V s = S::zero();
 #pragma unroll
   for (int dy = -(RHO - 1); dy <= RHO - 1; ++dy) {
     V sx = S::zero();
 #pragma unroll
     for (int dx = -(RHO - 1); dx <= RHO - 1; ++dx)
-      sx += S::ld(yf, unit, nvf, c0 + dy * Wf + dx) * float(RHO - (dx < 0 ? -dx : dx));
+      sx += S::ldv(yb, nvf, c0 + dy * Wf + dx) * float(RHO - (dx < 0 ? -dx : dx));
     s += sx * float(RHO - (dy < 0 ? -dy : dy));
   }
   o[k] = scale * S::to(s) * (1.0 / (RHO * RHO));
@@ -245,6 +252,7 @@ __global__ void k_prolong_add2d(int nf, const double *xc, int nvc, double *phif,
   const double *x = xc + (size_t)unit * nvc + Kx + Wc * Ky;
   const V x00 = S::from(x[0]), x10 = S::from(x[1]), x01 = S::from(x[Wc]), x11 = S::from(x[Wc + 1]);
   const int f0 = (Ky * RHO) * Wf + Kx * RHO;
+  const typename S::P pf = S::vec(phif, unit, nvf);
   const V dl = x01 - x00, dr = x11 - x10;
 #pragma unroll
   for (int j = 0; j < RHO; ++j) {
@@ -254,7 +262,7 @@ __global__ void k_prolong_add2d(int nf, const double *xc, int nvc, double *phif,
 #pragma unroll
     for (int i = 0; i < RHO; ++i) {
       const int k = f0 + j * Wf + i;
-      S::st(phif, unit, nvf, k, S::ld(phif, unit, nvf, k) + (aj + dj * (float(i) * (1.0f / RHO))));
+      S::stv(pf, nvf, k, S::ldv(pf, nvf, k) + (aj + dj * (float(i) * (1.0f / RHO))));
     }
   }
 }
