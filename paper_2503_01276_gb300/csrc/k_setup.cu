@@ -8,13 +8,13 @@
 // 4 * #elements, for phi_j^m it is 4 * sum over the row's elements of (centroid_m - c_mj).
 //
 // The setup also forms S = Ct M^-1 Ct^T with M = diag(A) (the Jacobi preconditioner) and
-// inverts it in FP64 (Cholesky, then L^-T L^-1). S^-1 is the small dense solve of the
+// inverts it in FP64 (Gauss-Jordan). S^-1 is the small dense solve of the
 // constraint projection used by the PCG and by the FP64 refinement. Rows of empty
 // (continuum, sub-block) pairs are decoupled with a unit diagonal, so their multiplier is 0.
 //
 // Two kernels: k_setup_nodes runs on (point, slice of node rows) and writes M^-1 and adds
 // its part of S and of the per-(continuum, sub-block) element counts and centroid sums to
-// zero-initialised accumulators; k_setup_point (one warp per point) forms the targets and
+// zero-initialised accumulators; k_setup_point (one CTA per point) forms the targets and
 // the inverse. M^-1 is an FP32 reciprocal refined by two FP64 Newton steps (a preconditioner
 // only needs a fixed positive diagonal; S and every later use read the same stored value).
 #include "common.cuh"
@@ -44,11 +44,11 @@ __global__ void __launch_bounds__(SN_THREADS) k_setup_nodes(SetupArgs a, int sli
   const int per = (n + 1 + slices - 1) / slices;
   const int y0 = slice * per, y1 = min(n + 1, y0 + per);
   __shared__ double S[MCH_MAX_NC * MCH_MAX_NC];
-  __shared__ double bs[MCH_MAX_NC * 3];
+  __shared__ int bsi[MCH_MAX_NC * 3];   // element count, sum of ex, sum of ey per row
   __shared__ int flags;
   if (tid == 0) flags = 0;
   for (int i = tid; i < nc * nc; i += SN_THREADS) S[i] = 0.0;
-  for (int i = tid; i < nc * 3; i += SN_THREADS) bs[i] = 0.0;
+  for (int i = tid; i < nc * 3; i += SN_THREADS) bsi[i] = 0;
   __syncthreads();
 
   // elements of the slice: validation, counts and centroid sums per (continuum, sub-block)
@@ -63,9 +63,9 @@ __global__ void __launch_bounds__(SN_THREADS) k_setup_nodes(SetupArgs a, int sli
     }
     const int ex = e % n, ey = e / n;
     const int b = l * nq + (ey / m) * P + ex / m;
-    atomicAdd(&bs[3 * b + 0], 1.0);
-    atomicAdd(&bs[3 * b + 1], -0.5 * a.len + (ex + 0.5) * a.h);
-    atomicAdd(&bs[3 * b + 2], -0.5 * a.len + (ey + 0.5) * a.h);
+    atomicAdd(&bsi[3 * b + 0], 1);
+    atomicAdd(&bsi[3 * b + 1], ex);
+    atomicAdd(&bsi[3 * b + 2], ey);
   }
   __syncthreads();
   if (flags) {
@@ -120,40 +120,52 @@ __global__ void __launch_bounds__(SN_THREADS) k_setup_nodes(SetupArgs a, int sli
   double *Sg = a.Sacc + (size_t)pt * nc * nc;
   for (int i = tid; i < nc * nc; i += SN_THREADS)
     if (S[i] != 0.0) atomicAdd(&Sg[i], S[i]);
+  // counts and centroid sums: sum over elements of (-len/2 + (e + 1/2) h) from the integer
+  // index sums (exact)
   double *bg = a.bacc + (size_t)pt * nc * 3;
-  for (int i = tid; i < nc * 3; i += SN_THREADS)
-    if (bs[i] != 0.0) atomicAdd(&bg[i], bs[i]);
+  for (int i = tid; i < nc * 3; i += SN_THREADS) {
+    const int b = i / 3, c = i % 3;
+    const int cnt = bsi[3 * b];
+    if (cnt == 0) continue;
+    const double v = c == 0 ? (double)cnt
+                            : (double)cnt * (-0.5 * a.len + 0.5 * a.h) + a.h * (double)bsi[i];
+    atomicAdd(&bg[i], v);
+  }
 }
 
-// One warp per point (several points per CTA): the small dense factorisation is a chain of
-// dependent column steps, so warp-synchronous steps replace block-wide barriers.
-__global__ void k_setup_point(SetupArgs a, int ppb) {
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int pt = blockIdx.x * ppb + wib;
+// One CTA per point. S^-1 by in-place Gauss-Jordan elimination, one thread per matrix entry:
+// nc pivot steps of fully parallel rank-one updates (S is symmetric positive definite, so the
+// diagonal pivots, the Schur-complement diagonals of the elimination, need no pivoting).
+constexpr int SP_THREADS = 1024;
+
+__global__ void __launch_bounds__(SP_THREADS) k_setup_point(SetupArgs a) {
+  const int pt = blockIdx.x;
   const int P = a.P, N = a.N, R = a.R, nc = a.nc;
   const int nq = P * P;
-  if (pt >= a.npts) return;
-  if (a.status[pt] & 3) return;  // uniform over the warp
+  const int tid = threadIdx.x;
+  if (a.status[pt] & 3) return;
 
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const size_t per = (size_t)2 * nc * nc + 4 * nc + 2 * MCH_MAX_CONT;
-  double *S = reinterpret_cast<double *>(smem_raw) + wib * per;  // [nc][nc]
-  double *Z = S + nc * nc;                                        // [nc][nc]
-  double *bs = Z + nc * nc;                                       // [nc][3] count, sum x, sum y
-  double *cen = bs + 3 * nc;                                      // [MCH_MAX_CONT][2]
-  double *dorig = cen + 2 * MCH_MAX_CONT;                         // [nc]
-  int flags = 0;
+  double *A = reinterpret_cast<double *>(smem_raw);      // [nc][nc], S then S^-1
+  double *bs = A + nc * nc;                               // [nc][3] count, sum x, sum y
+  double *cen = bs + 3 * nc;                              // [MCH_MAX_CONT][2]
+  double *dorig = cen + 2 * MCH_MAX_CONT;                 // [nc]
+  double *col = dorig + nc;                               // [nc] pivot column of a step
+  double *rowk = col + nc;                                // [nc] pivot row of a step
+  __shared__ int flags;
+  __shared__ double rpiv;
+  if (tid == 0) flags = 0;
   const double *Sg = a.Sacc + (size_t)pt * nc * nc;
-  for (int i = lane; i < nc * nc; i += 32) S[i] = Sg[i];
-  for (int i = lane; i < 3 * nc; i += 32) bs[i] = a.bacc[(size_t)pt * nc * 3 + i];
-  __syncwarp();
+  for (int i = tid; i < nc * nc; i += SP_THREADS) A[i] = Sg[i];
+  for (int i = tid; i < 3 * nc; i += SP_THREADS) bs[i] = a.bacc[(size_t)pt * nc * 3 + i];
+  __syncthreads();
 
   // centroids c_mj over the integration region R_p (the central (P - 2 overs)^2 periods;
   // the whole RVE when the continuum is absent there, or when overs = 0)
-  if (lane < N) {
+  if (tid < N) {
     double c = 0, x = 0, y = 0, ca = 0, xa = 0, ya = 0;
     for (int q = 0; q < nq; ++q) {
-      const int b = lane * nq + q;
+      const int b = tid * nq + q;
       const int qx = q % P, qy = q / P;
       ca += bs[3 * b];
       xa += bs[3 * b + 1];
@@ -164,20 +176,20 @@ __global__ void k_setup_point(SetupArgs a, int ppb) {
         y += bs[3 * b + 2];
       }
     }
-    if (ca == 0.0) flags |= 8;
+    if (ca == 0.0) atomicOr(&flags, 8);
     if (c == 0.0) {
       c = ca;
       x = xa;
       y = ya;
     }
-    cen[2 * lane] = c > 0 ? x / c : 0.0;
-    cen[2 * lane + 1] = c > 0 ? y / c : 0.0;
+    cen[2 * tid] = c > 0 ? x / c : 0.0;
+    cen[2 * tid + 1] = c > 0 ? y / c : 0.0;
   }
-  __syncwarp();
+  __syncthreads();
 
   // scaled targets G[b][r]
   double *G = a.G + (size_t)pt * nc * R;
-  for (int t = lane; t < nc * R; t += 32) {
+  for (int t = tid; t < nc * R; t += SP_THREADS) {
     const int b = t / R, r = t % R;
     const int j = b / nq;
     double v = 0.0;
@@ -189,55 +201,53 @@ __global__ void k_setup_point(SetupArgs a, int ppb) {
     }
     G[t] = v;
   }
-  for (int i = lane; i < nc; i += 32) {
-    if (bs[3 * i] == 0.0) S[i * nc + i] = 1.0;
-    dorig[i] = S[i * nc + i];
+  if (tid < nc) {
+    if (bs[3 * tid] == 0.0) A[tid * nc + tid] = 1.0;
+    dorig[tid] = A[tid * nc + tid];
   }
-  __syncwarp();
+  __syncthreads();
 
-  // Cholesky S = L L^T in place (lower triangle)
+  // Gauss-Jordan: after step k, row k holds e_k^T times the running inverse
   for (int k = 0; k < nc; ++k) {
-    if (lane == 0) {
-      double v = S[k * nc + k];
+    if (tid == 0) {
+      double v = A[k * nc + k];
       if (!(v > 1e-13 * dorig[k])) {
         flags |= 4;
         v = dorig[k] > 0 ? dorig[k] : 1.0;
       }
-      S[k * nc + k] = sqrt(v);
+      rpiv = 1.0 / v;
     }
-    __syncwarp();
-    const double dkk = S[k * nc + k];
-    for (int i = k + 1 + lane; i < nc; i += 32) S[i * nc + k] /= dkk;
-    __syncwarp();
-    const int rem = nc - k - 1;
-    for (int t = lane; t < rem * rem; t += 32) {
-      const int i = k + 1 + t / rem, j = k + 1 + t % rem;
-      if (j <= i) S[i * nc + j] -= S[i * nc + k] * S[j * nc + k];
+    // snapshot the pivot column and row: the update below overwrites both
+    for (int i = tid; i < nc; i += SP_THREADS) {
+      col[i] = A[i * nc + k];
+      rowk[i] = A[k * nc + i];
     }
-    __syncwarp();
+    __syncthreads();
+    const double rp = rpiv;
+    for (int t = tid; t < nc * nc; t += SP_THREADS) {
+      const int i = t / nc, j = t % nc;
+      // pivot row: A[k][j] / p (the pivot entry itself becomes 1 / p)
+      const double akj = (j == k ? 1.0 : rowk[j]) * rp;
+      if (i == k) {
+        A[t] = akj;
+      } else {
+        const double f = col[i];
+        A[t] = (j == k ? 0.0 : A[t]) - f * akj;
+      }
+    }
+    __syncthreads();
   }
 
-  // Z = L^-1 (column j by forward substitution), then S^-1 = Z^T Z
-  for (int j = lane; j < nc; j += 32) {
-    for (int i = 0; i < nc; ++i) {
-      double v = (i == j) ? 1.0 : 0.0;
-      if (i > j)
-        for (int k = j; k < i; ++k) v -= S[i * nc + k] * Z[k * nc + j];
-      Z[i * nc + j] = (i < j) ? 0.0 : v / S[i * nc + i];
-    }
-  }
-  __syncwarp();
   double *Si64 = a.Sinv64 + (size_t)pt * nc * nc;
   float *Si32 = a.Sinv32 ? a.Sinv32 + (size_t)pt * nc * nc : nullptr;
-  for (int t = lane; t < nc * nc; t += 32) {
+  for (int t = tid; t < nc * nc; t += SP_THREADS) {
+    // symmetrise (the elimination leaves round-off asymmetry)
     const int i = t / nc, j = t % nc;
-    double v = 0.0;
-    for (int k = max(i, j); k < nc; ++k) v += Z[k * nc + i] * Z[k * nc + j];
+    const double v = 0.5 * (A[t] + A[j * nc + i]);
     Si64[t] = v;
     if (Si32) Si32[t] = (float)v;
   }
-  flags = __reduce_or_sync(0xffffffffu, flags);
-  if (lane == 0) {
+  if (tid == 0) {
     int nd = 0;
     for (int b = 0; b < nc; ++b) nd += (bs[3 * b] == 0.0);
     a.dropped[pt] = nd;
@@ -258,15 +268,12 @@ cudaError_t launch_setup2d(const SetupArgs &a, cudaStream_t st) {
   k_setup_nodes<<<dim3(a.npts, slices), SN_THREADS, 0, st>>>(a, slices);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const size_t per = sizeof(double) * (2 * (size_t)a.nc * a.nc + 4 * a.nc + 2 * MCH_MAX_CONT);
-  int ppb = (int)((96 * 1024) / per);
-  ppb = ppb < 1 ? 1 : (ppb > 4 ? 4 : ppb);
-  const size_t smem = per * ppb;
+  const size_t smem = sizeof(double) * ((size_t)a.nc * a.nc + 6 * a.nc + 2 * MCH_MAX_CONT);
   if (smem > 48 * 1024) {
     e = cudaFuncSetAttribute(k_setup_point, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_setup_point<<<(a.npts + ppb - 1) / ppb, 32 * ppb, smem, st>>>(a, ppb);
+  k_setup_point<<<a.npts, SP_THREADS, smem, st>>>(a);
   return cudaGetLastError();
 }
 
