@@ -45,7 +45,7 @@ sys.path.insert(0, ROOT)
 import mch_inputs as mi  # noqa: E402
 
 METRIC = "cell-problem RHS solved/s at 1e-6 rel. accuracy; stencil HBM GB/s vs peak"
-WORKLOAD = "channel2d_17x17_L3"
+WORKLOAD = "channel2d_17x17_L3"   # the benchmark workload (--workload selects others)
 # algorithmic FP32 flops of one PCG iteration per interior node: stencil 17, four dot
 # products 8, x/r/p updates 6, M^-1 r and M^-1 q 2, Ct^T lambda gather 4, two Ct scatters 8
 FLOPS_PER_NODE_ITER = 45
@@ -55,8 +55,8 @@ SMS, FP32_LANES = 152, 128
 #   python bench.py --steps 1 --warmup 3 --no-cpu --no-plain
 # Valid only for the kernel source it was taken on: the JSON reports null when the
 # sources' hash differs.
-LEVEL_TRAFFIC = {"sha256_16": ("fdbff188de809e3d", "7fb67ff164f56870"),
-                 "bytes_per_launch": (2.83136e6, 20.28083e6, 16.80358e6)}
+LEVEL_TRAFFIC = {"sha256_16": ("43c91844b0a8140f", "3e24044d01b04bd2", "d8d56e737f1a3b53"),
+                 "bytes_per_launch": (2.832128e6, 20.505088e6, 16.83456e6)}
 
 
 class ClockSampler:
@@ -110,7 +110,7 @@ class ClockSampler:
 def _level_traffic():
     import hashlib
     got = []
-    for f in ("k_level.cuh", "k_level_f32.cu"):
+    for f in ("k_level.cuh", "k_level_f32.cu", "k_level_f32_alt.cu"):
         with open(os.path.join(ROOT, "paper_2503_01276_gb300", "csrc", f), "rb") as fh:
             got.append(hashlib.sha256(fh.read()).hexdigest()[:16])
     if tuple(got) != LEVEL_TRAFFIC["sha256_16"]:
@@ -205,7 +205,8 @@ def run_reference(args, rank, world):
         env.pop(k, None)
 
     def leg():
-        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-leg", ""],
+        out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-leg", "",
+                              "--workload", args.workload],
                              capture_output=True, text=True, env=env, timeout=600)
         return json.loads(out.stdout.strip().splitlines()[-1])["cpu"]
 
@@ -213,7 +214,7 @@ def run_reference(args, rank, world):
         leg()
     legs = [leg() for _ in range(args.steps)]
     v = float(np.mean([c["value"] for c in legs]))
-    wl = mi.workload(WORKLOAD)
+    wl = mi.workload(args.workload)
     rhs_per_step = sum(_level_sizes(wl)) * wl.n_rhs
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "RHS/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -232,7 +233,8 @@ def _level_sizes(wl):
 
 
 def _config(wl, precision):
-    return {"workload": WORKLOAD, "macropoints": f"{wl.macro_n}x{wl.macro_n}",
+    return {"workload": wl.name,
+            "macropoints": "x".join([str(wl.macro_n)] * wl.dim),
             "levels": _level_sizes(wl), "rve_grids": [wl.n_level(k + 1) for k in range(wl.n_levels)],
             "rhs_per_point": wl.n_rhs, "contrast": wl.contrast, "precision": precision,
             "l2": "flushed before every timed step (512 MB write, untimed)"}
@@ -289,6 +291,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline leg")
     ap.add_argument("--no-plain", action="store_true",
                     help="skip the unbatched per-macropoint FP64 comparator")
+    ap.add_argument("--workload", default=WORKLOAD,
+                    help="workload of mch_inputs (default: the benchmark workload)")
     ap.add_argument("--tiles", default=None,
                     help="comma-separated launch shapes per level instead of autotuning "
                          "(fixed launch counts, for profiling)")
@@ -300,7 +304,7 @@ def main():
         if args.cpu_leg:
             z = np.load(args.cpu_leg)
             Eg = [z[f"E{i}"] for i in range(len(z.files))]
-        cb, err = cpu_baseline(mi.workload(WORKLOAD, precision=args.precision), Eg)
+        cb, err = cpu_baseline(mi.workload(args.workload, precision=args.precision), Eg)
         print(json.dumps({"cpu": cb, "err": err}), flush=True)
         return
 
@@ -319,7 +323,8 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     dev = torch.device("cuda", local)
-    wl = mi.workload(WORKLOAD, precision=args.precision, seed=mi.workload(WORKLOAD).seed + rank)
+    wl = mi.workload(args.workload, precision=args.precision,
+                     seed=mi.workload(args.workload).seed + rank)
     stream = torch.cuda.current_stream()
     s = mch.Solver.from_workload(wl, stream=stream.cuda_stream)
     s.set_timing(True)
@@ -425,7 +430,8 @@ def main():
     fp32_peak = SMS * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
     pcg_flops = pcg_node_iters * FLOPS_PER_NODE_ITER
     achieved = pcg_flops / (pcg_ms / 1e3) / 1e12 if pcg_ms > 0 else None
-    traffic, traffic_levels = _level_traffic() if args.precision == "mixed" else (None, None)
+    traffic, traffic_levels = ((_level_traffic() if args.precision == "mixed" and
+                                wl.name == WORKLOAD and tiles == [0, 1, 1] else (None, None)))
     roofline = {"bound": "alu", "kernel": "k_level2d (persistent level solve)",
                 "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                 "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,
@@ -435,7 +441,7 @@ def main():
                 "kernel_share_of_step": (pcg_ms / (t_total * 1e3)) if t_total > 0 else None,
                 "launches_timed": pcg_launches}
     plain = None
-    if not args.no_plain:
+    if not args.no_plain and wl.dim == 2:
         plain, E_plain = plain_fp64_leg(wl, med_dev, flush, 2, stream)
         plain["speedup_of_value"] = value / world / plain["value"]
         sys.path.insert(0, os.path.join(ROOT, "tests"))
@@ -456,8 +462,8 @@ def main():
             for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
                 env.pop(k, None)
             out = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-leg", fn,
-                                  "--precision", args.precision], capture_output=True, text=True,
-                                 env=env, timeout=600)
+                                  "--precision", args.precision, "--workload", args.workload],
+                                 capture_output=True, text=True, env=env, timeout=600)
             try:
                 res = json.loads(out.stdout.strip().splitlines()[-1])
                 cpu, acc_err = res["cpu"], res["err"]
