@@ -50,6 +50,12 @@ WORKLOAD = "channel2d_17x17_L3"   # the benchmark workload (--workload selects o
 # products 8, x/r/p updates 6, M^-1 r and M^-1 q 2, Ct^T lambda gather 4, two Ct scatters 8
 FLOPS_PER_NODE_ITER = 45
 SMS, FP32_LANES = 152, 128
+# algorithmic HBM bytes of one inner PCG iteration of the 3D level kernel per interior node of
+# a (point, function) unit, FP32 vectors: q = A p pass reads p and r and writes q (12 B); the
+# update pass reads p, q and r, reads and writes delta and r, writes p (28 B); per-point data
+# (kappa 4 B, labels 1 B and M^-1 4 B in the first pass, labels and M^-1 in the second: 14 B)
+# is shared by the point's R functions
+BYTES3D_PER_NODE_ITER_UNIT, BYTES3D_PER_NODE_ITER_POINT = 40, 14
 # DRAM bytes (read + write) per k_level2d launch of this workload (levels 1, 2, 3), from one
 # ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of
 #   python bench.py --steps 1 --warmup 3 --no-cpu --no-plain
@@ -432,14 +438,27 @@ def main():
     achieved = pcg_flops / (pcg_ms / 1e3) / 1e12 if pcg_ms > 0 else None
     traffic, traffic_levels = ((_level_traffic() if args.precision == "mixed" and
                                 wl.name == WORKLOAD and tiles == [0, 1, 1] else (None, None)))
-    roofline = {"bound": "alu", "kernel": "k_level2d (persistent level solve)",
-                "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,
-                "traffic_per_launch_by_level": traffic_levels,
-                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x median sampled SM clock",
-                "flops_per_node_iteration": FLOPS_PER_NODE_ITER,
-                "kernel_share_of_step": (pcg_ms / (t_total * 1e3)) if t_total > 0 else None,
-                "launches_timed": pcg_launches}
+    share = (pcg_ms / (t_total * 1e3)) if t_total > 0 else None
+    if wl.dim == 2:
+        roofline = {"bound": "alu", "kernel": "k_level2d (persistent level solve)",
+                    "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                    "frac": (achieved / fp32_peak) if achieved else None, "traffic": traffic,
+                    "traffic_per_launch_by_level": traffic_levels,
+                    "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x median sampled SM clock",
+                    "flops_per_node_iteration": FLOPS_PER_NODE_ITER,
+                    "kernel_share_of_step": share, "launches_timed": pcg_launches}
+    else:
+        # the 3D level kernel streams its vectors through HBM: bytes of the inner iterations
+        bpn = BYTES3D_PER_NODE_ITER_UNIT + BYTES3D_PER_NODE_ITER_POINT / s.R
+        gbs = pcg_node_iters * bpn / (pcg_ms / 1e3) / 1e9 if pcg_ms > 0 else None
+        hbm = peaks.get("hbm_gbs")
+        roofline = {"bound": "hbm", "kernel": "k_level3d (cooperative level solve)",
+                    "achieved": gbs, "peak": hbm or 6800.0, "unit": "GB/s",
+                    "frac": (gbs / (hbm or 6800.0)) if gbs else None, "traffic": None,
+                    "peak_source": ("measured copy bandwidth" if hbm else
+                                    "fallback 6.8 TB/s"),
+                    "bytes_per_node_iteration": bpn,
+                    "kernel_share_of_step": share, "launches_timed": pcg_launches}
     plain = None
     if not args.no_plain and wl.dim == 2:
         plain, E_plain = plain_fp64_leg(wl, med_dev, flush, 2, stream)

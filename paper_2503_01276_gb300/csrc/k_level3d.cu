@@ -84,43 +84,61 @@ __device__ __forceinline__ void load_lplane(int (&l)[2][2], const uint8_t *lab, 
 }
 
 // Per-column accumulation of node values into the constraint rows of the adjacent elements
-// (node-based form of Ct v): the four element columns (sx, sy) around the node column keep
-// per-label partial sums for the current z-block and flush them to shared memory.
-template <typename V, int NCN>
+// (node-based form of Ct v): each of the four element columns (sx, sy) around the node column
+// keeps one partial sum for its current label and z-block; a change of label or of z-block
+// flushes it to shared memory (labels change rarely along a column).
+template <typename V>
 struct ColBins {
-  V acc[4][NCN];
+  V acc[4];
+  int lab[4];
   int zb;
-  __device__ __forceinline__ void reset() {
+  double *bins;
+  int nq, m, P, kx, ky;
+  __device__ __forceinline__ void init(double *b, int kx_, int ky_, int m_, int P_, int nq_) {
+    bins = b;
+    kx = kx_;
+    ky = ky_;
+    m = m_;
+    P = P_;
+    nq = nq_;
+    zb = 0;
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int j = 0; j < NCN; ++j) acc[c][j] = V(0);
+    for (int c = 0; c < 4; ++c) {
+      acc[c] = V(0);
+      lab[c] = -1;
+    }
+  }
+  __device__ __forceinline__ void flush_one(int c) {
+    if (lab[c] >= 0 && acc[c] != V(0)) {
+      const int ex = kx - 1 + (c & 1), ey = ky - 1 + (c >> 1);
+      atomicAdd(&bins[lab[c] * nq + (zb * P + ey / m) * P + ex / m], (double)acc[c]);
+    }
+    acc[c] = V(0);
   }
   __device__ __forceinline__ void add(const int (&l)[2][2], V v) {
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
-#pragma unroll
-      for (int j = 0; j < NCN; ++j) acc[c][j] += (l[c >> 1][c & 1] == j) ? v : V(0);
-  }
-  __device__ __forceinline__ void flush(double *bins, int kx, int ky, int m, int P, int nq) {
-#pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int ex = kx - 1 + (c & 1), ey = ky - 1 + (c >> 1);
-      const int base = (zb * P + ey / m) * P + ex / m;
-#pragma unroll
-      for (int j = 0; j < NCN; ++j)
-        if (acc[c][j] != V(0)) atomicAdd(&bins[j * nq + base], (double)acc[c][j]);
+      const int lc = l[c >> 1][c & 1];
+      if (lc != lab[c]) {
+        flush_one(c);
+        lab[c] = lc;
+      }
+      acc[c] += v;
     }
-    reset();
+  }
+  // all partial sums out (at a z-block boundary and at the end of the column)
+  __device__ __forceinline__ void flush() {
+#pragma unroll
+    for (int c = 0; c < 4; ++c) flush_one(c);
   }
 };
 
 // Ct^T vec at a node from the labels of its 8 adjacent elements (lower plane ez = kz-1,
 // upper plane ez = kz).
-__device__ __forceinline__ double ctt_node(const double *vec, const int (&lo)[2][2],
-                                           const int (&up)[2][2], int kx, int ky, int kz, int m,
-                                           int P, int nq) {
-  double s = 0.0;
+template <typename V>
+__device__ __forceinline__ V ctt_node(const V *vec, const int (&lo)[2][2], const int (&up)[2][2],
+                                      int kx, int ky, int kz, int m, int P, int nq) {
+  V s = 0;
   const int zl = (kz - 1) / m, zu = kz / m;
 #pragma unroll
   for (int sy = 0; sy < 2; ++sy)
@@ -137,7 +155,7 @@ struct Col {
   int u, slot, pt, kx, ky;
 };
 
-template <typename T, int NCN>
+template <typename T>
 __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
   cg::grid_group grid = cg::this_grid();
   const int n = a.n, W = n + 1, ni = n - 1, R = a.R, nc = a.nc, P = a.P, m = a.m;
@@ -186,6 +204,9 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
     ip += km;
     S.sweeps = ip;
   }
+  // multipliers of the inner update pass in the inner precision: they live in the second half
+  // of the slot's bins, which that pass does not use (it is cleared before the next q = A p)
+  auto vecT = [&](int s) { return reinterpret_cast<T *>(S.bins + (size_t)s * 2 * nc + nc); };
   for (int s = tid; s < K; s += L3_THREADS) {
     S.flags[s] = 0;
     S.iters[s] = 0;
@@ -261,12 +282,10 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
       if (S.flags[cl.slot] & F_DONE) continue;
       const size_t ub = (size_t)cl.u * a.nv + cl.kx + (size_t)W * cl.ky;
       const uint8_t *lab = a.labels + (size_t)cl.pt * n * n * n;
-      ColBins<double, NCN> cb;
-      cb.reset();
-      cb.zb = 0;
+      ColBins<double> cb;
+      cb.init(S.bins + cl.slot * 2 * nc, cl.kx, cl.ky, m, P, nq);
       int lo[2][2], up[2][2];
       load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
-      double *sb = S.bins + cl.slot * 2 * nc;
       for (int kz = 1; kz < n; ++kz) {
         load_lplane(up, lab, cl.kx, cl.ky, kz, n, a.N - 1);
         const size_t o = ub + W2 * kz;
@@ -278,7 +297,7 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
         }
         cb.add(lo, xv);
         if (kz % m == 0) {
-          cb.flush(sb, cl.kx, cl.ky, m, P, nq);
+          cb.flush();
           cb.zb = kz / m;
         }
         cb.add(up, xv);
@@ -287,7 +306,7 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
 #pragma unroll
           for (int j = 0; j < 2; ++j) lo[i][j] = up[i][j];
       }
-      cb.flush(sb, cl.kx, cl.ky, m, P, nq);
+      cb.flush();
     }
     __syncthreads();
     push_local(nc);
@@ -345,10 +364,8 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
       load_kplane(k[0], kap, cl.kx, cl.ky, 0, n);
       int lo[2][2], up[2][2];
       load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
-      ColBins<double, NCN> cb;
-      cb.reset();
-      cb.zb = 0;
-      double *sb = S.bins + cl.slot * 2 * nc;
+      ColBins<double> cb;
+      cb.init(S.bins + cl.slot * 2 * nc, cl.kx, cl.ky, m, P, nq);
       for (int kz = 1; kz < n; ++kz) {
         load_plane9(v[2], a.x, ub + W2 * (kz + 1), W);
         load_kplane(k[1], kap, cl.kx, cl.ky, kz, n);
@@ -360,7 +377,7 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
         const double mr = a.minv64[mb + W2 * kz] * r;
         cb.add(lo, mr);
         if (kz % m == 0) {
-          cb.flush(sb, cl.kx, cl.ky, m, P, nq);
+          cb.flush();
           cb.zb = kz / m;
         }
         cb.add(up, mr);
@@ -379,7 +396,7 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
             lo[i][j] = up[i][j];
           }
       }
-      cb.flush(sb, cl.kx, cl.ky, m, P, nq);
+      cb.flush();
     }
     __syncthreads();
     push_local(nc);
@@ -480,12 +497,11 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
         load_kplane(k[0], kap, cl.kx, cl.ky, 0, n);
         int lo[2][2], up[2][2];
         load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
-        ColBins<T, NCN> bz, bq;
-        bz.reset();
-        bq.reset();
-        bz.zb = bq.zb = 0;
-        T pq = 0, zq = 0, qmq = 0, rz = 0;
+        ColBins<T> bz, bq;
         double *sb = S.bins + cl.slot * 2 * nc;
+        bz.init(sb, cl.kx, cl.ky, m, P, nq);
+        bq.init(sb + nc, cl.kx, cl.ky, m, P, nq);
+        T pq = 0, zq = 0, qmq = 0, rz = 0;
         const T hT = (T)a.h;
         for (int kz = 1; kz < n; ++kz) {
           load_plane9(v[2], a.p, ub + W2 * (kz + 1), W);
@@ -504,8 +520,8 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
           bz.add(lo, z);
           bq.add(lo, qm);
           if (kz % m == 0) {
-            bz.flush(sb, cl.kx, cl.ky, m, P, nq);
-            bq.flush(sb + nc, cl.kx, cl.ky, m, P, nq);
+            bz.flush();
+            bq.flush();
             bz.zb = bq.zb = kz / m;
           }
           bz.add(up, z);
@@ -525,8 +541,8 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
               lo[i][j] = up[i][j];
             }
         }
-        bz.flush(sb, cl.kx, cl.ky, m, P, nq);
-        bq.flush(sb + nc, cl.kx, cl.ky, m, P, nq);
+        bz.flush();
+        bq.flush();
         double *ss = S.sums + cl.slot * 8;
         atomicAdd(&ss[0], (double)pq);
         atomicAdd(&ss[1], (double)zq);
@@ -559,6 +575,7 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
             T l = 0;
             for (int j = 0; j < nc; ++j) l += Si[(size_t)j * nc + i] * (T)S.bins[s * 2 * nc + j];
             S.vec[s * nc + i] = (double)l;
+            vecT(s)[i] = l;
           }
           __syncthreads();
           if (tid == 0) {
@@ -589,7 +606,7 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
         const size_t ub = (size_t)cl.u * a.nv + cl.kx + (size_t)W * cl.ky;
         const size_t mb = (size_t)cl.pt * a.nv + cl.kx + (size_t)W * cl.ky;
         const uint8_t *lab = a.labels + (size_t)cl.pt * n * n * n;
-        const double *vec = S.vec + cl.slot * nc;
+        const T *vec = vecT(cl.slot);
         const T al = (T)S.alpha[cl.slot], be = (T)S.beta[cl.slot];
         int lo[2][2], up[2][2];
         load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
@@ -598,7 +615,7 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
           const size_t o = ub + W2 * kz;
           const T p = a.p[o];
           a.d[o] += al * p;
-          const T r = a.r[o] - al * a.q[o] - (T)ctt_node(vec, lo, up, cl.kx, cl.ky, kz, m, P, nq);
+          const T r = a.r[o] - al * a.q[o] - ctt_node(vec, lo, up, cl.kx, cl.ky, kz, m, P, nq);
           a.r[o] = r;
           if (!(f & 8)) a.p[o] = a.minvT[mb + W2 * kz] * r + be * p;
 #pragma unroll
@@ -638,7 +655,7 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
   }
 }
 
-template <typename T, int NCN>
+template <typename T>
 cudaError_t launch3(const Level3Args<T> &a0, cudaStream_t st) {
   Level3Args<T> a = a0;
   const long long cpu = (long long)(a.n - 1) * (a.n - 1);
@@ -655,10 +672,10 @@ cudaError_t launch3(const Level3Args<T> &a0, cudaStream_t st) {
   int grid = 0;
   for (int kmax = 2; kmax <= 64; kmax *= 2) {
     const size_t smem = smem_for(kmax);
-    e = cudaFuncSetAttribute(k_level3d<T, NCN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(k_level3d<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_level3d<T, NCN>, L3_THREADS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_level3d<T>, L3_THREADS, smem);
     if (e != cudaSuccess) return e;
     if (occ < 1) return cudaErrorInvalidConfiguration;
     grid = occ * sms;
@@ -670,7 +687,7 @@ cudaError_t launch3(const Level3Args<T> &a0, cudaStream_t st) {
       a.cols_per_cta = per;
       grid = (int)((total + per - 1) / per);
       void *args[] = {&a};
-      return cudaLaunchCooperativeKernel((const void *)k_level3d<T, NCN>, dim3(grid),
+      return cudaLaunchCooperativeKernel((const void *)k_level3d<T>, dim3(grid),
                                          dim3(L3_THREADS), args, smem, st);
     }
   }
@@ -682,8 +699,7 @@ cudaError_t launch3(const Level3Args<T> &a0, cudaStream_t st) {
 template <typename T>
 cudaError_t launch_level3d(const Level3Args<T> &a, cudaStream_t st) {
   if (a.nc > MCH_MAX_NC3 || a.n < 2 || a.n % a.P || a.m != a.n / a.P) return cudaErrorInvalidValue;
-  if (a.N <= 2) return launch3<T, 2>(a, st);
-  return launch3<T, 4>(a, st);
+  return launch3<T>(a, st);
 }
 
 template cudaError_t launch_level3d<float>(const Level3Args<float> &, cudaStream_t);
