@@ -87,21 +87,46 @@ __device__ __forceinline__ void load_lplane(int (&l)[2][2], const uint8_t *lab, 
 // (node-based form of Ct v): each of the four element columns (sx, sy) around the node column
 // keeps one partial sum for its current label and z-block; a change of label or of z-block
 // flushes it to shared memory (labels change rarely along a column).
+// Sub-block offsets along a node column, advanced without divisions: for node kz, lo and up
+// are (z-block of the element plane below, resp. above) * P^2, and boundary() says that kz is
+// a multiple of m (the two planes lie in different z-blocks).
+struct ZBlk {
+  int rem, lo, up, m, pp;
+  __device__ __forceinline__ void init(int m_, int pp_) {  // kz = 1
+    m = m_;
+    pp = pp_;
+    rem = m_ == 1 ? 0 : 1;
+    lo = 0;
+    up = m_ == 1 ? pp_ : 0;
+  }
+  __device__ __forceinline__ bool boundary() const { return rem == 0; }
+  __device__ __forceinline__ void next() {  // kz -> kz + 1
+    lo = up;
+    if (++rem == m) {
+      rem = 0;
+      up += pp;
+    }
+  }
+};
+
+// Per-column accumulation of node values into the constraint rows of the adjacent elements
+// (node-based form of Ct v): each of the four element columns c = 2 sy + sx around the node
+// column keeps one partial sum for its current label and z-block; a change of label or of
+// z-block flushes it to shared memory (labels change rarely along a column). bxy[c] is the
+// element column's sub-block index within a z-block, zoff the current z-block * P^2.
 template <typename V>
 struct ColBins {
   V acc[4];
   int lab[4];
-  int zb;
+  int zoff;
   double *bins;
-  int nq, m, P, kx, ky;
-  __device__ __forceinline__ void init(double *b, int kx_, int ky_, int m_, int P_, int nq_) {
+  const int *bxy;
+  int nq;
+  __device__ __forceinline__ void init(double *b, const int *bxy_, int nq_) {
     bins = b;
-    kx = kx_;
-    ky = ky_;
-    m = m_;
-    P = P_;
+    bxy = bxy_;
     nq = nq_;
-    zb = 0;
+    zoff = 0;
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
       acc[c] = V(0);
@@ -109,10 +134,7 @@ struct ColBins {
     }
   }
   __device__ __forceinline__ void flush_one(int c) {
-    if (lab[c] >= 0 && acc[c] != V(0)) {
-      const int ex = kx - 1 + (c & 1), ey = ky - 1 + (c >> 1);
-      atomicAdd(&bins[lab[c] * nq + (zb * P + ey / m) * P + ex / m], (double)acc[c]);
-    }
+    if (lab[c] >= 0 && acc[c] != V(0)) atomicAdd(&bins[lab[c] * nq + zoff + bxy[c]], (double)acc[c]);
     acc[c] = V(0);
   }
   __device__ __forceinline__ void add(const int (&l)[2][2], V v) {
@@ -133,26 +155,115 @@ struct ColBins {
   }
 };
 
-// Ct^T vec at a node from the labels of its 8 adjacent elements (lower plane ez = kz-1,
-// upper plane ez = kz).
+// Ct^T vec at a node from the labels of its 8 adjacent elements (lower plane ez = kz-1 in the
+// z-block at offset zlo, upper plane ez = kz at zup).
 template <typename V>
 __device__ __forceinline__ V ctt_node(const V *vec, const int (&lo)[2][2], const int (&up)[2][2],
-                                      int kx, int ky, int kz, int m, int P, int nq) {
+                                      const int (&bxy)[4], int zlo, int zup, int nq) {
   V s = 0;
-  const int zl = (kz - 1) / m, zu = kz / m;
 #pragma unroll
-  for (int sy = 0; sy < 2; ++sy)
-#pragma unroll
-    for (int sx = 0; sx < 2; ++sx) {
-      const int bxy = ((ky - 1 + sy) / m) * P + (kx - 1 + sx) / m;
-      s += vec[lo[sy][sx] * nq + zl * P * P + bxy] + vec[up[sy][sx] * nq + zu * P * P + bxy];
-    }
+  for (int c = 0; c < 4; ++c)
+    s += vec[lo[c >> 1][c & 1] * nq + zlo + bxy[c]] + vec[up[c >> 1][c & 1] * nq + zup + bxy[c]];
   return s;
+}
+
+// The two passes of an inner iteration over one node column (kz = 1..n-1) of a unit. The
+// vectors are passed as restrict-qualified pointers to the column's base so that the loads of
+// the next z step may be issued ahead of the stores of the current one.
+
+// q = h A p; the column's sums p.q, z.q, q.M^-1 q, r.z (z = M^-1 r) and its constraint
+// functionals Ct z, Ct M^-1 q into the bins.
+template <typename T>
+__device__ __forceinline__ void p1_column(const T *__restrict__ p, T *__restrict__ q,
+                                          const T *__restrict__ rv, const T *__restrict__ mi,
+                                          const T *__restrict__ kap,
+                                          const uint8_t *__restrict__ lab, int n, int kx, int ky,
+                                          int m, int pp, int nm1, T h, ColBins<T> &bz,
+                                          ColBins<T> &bq, T (&sum)[4]) {
+  const int W = n + 1, W2 = W * W;
+  T v[3][3][3], k[2][2][2];
+  load_plane9(v[0], p, 0, W);
+  load_plane9(v[1], p, W2, W);
+  load_kplane(k[0], kap, kx, ky, 0, n);
+  int lo[2][2], up[2][2];
+  load_lplane(lo, lab, kx, ky, 0, n, nm1);
+  ZBlk zb;
+  zb.init(m, pp);
+  for (int kz = 1; kz < n; ++kz, zb.next()) {
+    load_plane9(v[2], p, (size_t)W2 * (kz + 1), W);
+    load_kplane(k[1], kap, kx, ky, kz, n);
+    load_lplane(up, lab, kx, ky, kz, n, nm1);
+    const int o = W2 * kz;
+    const T qv = h * q1_apply3d<T>(v, k);
+    q[o] = qv;
+    const T mv = mi[o], r = rv[o];
+    const T z = mv * r, qm = mv * qv;
+    sum[0] += v[1][1][1] * qv;
+    sum[1] += z * qv;
+    sum[2] += qv * qm;
+    sum[3] += r * z;
+    bz.add(lo, z);
+    bq.add(lo, qm);
+    if (zb.boundary()) {
+      bz.flush();
+      bq.flush();
+      bz.zoff = bq.zoff = zb.up;
+    }
+    bz.add(up, z);
+    bq.add(up, qm);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        v[0][i][j] = v[1][i][j];
+        v[1][i][j] = v[2][i][j];
+      }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        k[0][i][j] = k[1][i][j];
+        lo[i][j] = up[i][j];
+      }
+  }
+  bz.flush();
+  bq.flush();
+}
+
+// delta += alpha p; r <- r - alpha q - Ct^T lambda; p = M^-1 r + beta p (unless last)
+template <typename T>
+__device__ __forceinline__ void p2_column(T *__restrict__ d, T *__restrict__ r,
+                                          T *__restrict__ p, const T *__restrict__ q,
+                                          const T *__restrict__ mi,
+                                          const uint8_t *__restrict__ lab,
+                                          const T *__restrict__ vec, int n, int kx, int ky,
+                                          const int (&bxy)[4], int m, int pp, int nq, int nm1,
+                                          T al, T be, bool last) {
+  const int W = n + 1, W2 = W * W;
+  int lo[2][2], up[2][2];
+  load_lplane(lo, lab, kx, ky, 0, n, nm1);
+  ZBlk zb;
+  zb.init(m, pp);
+#pragma unroll 4
+  for (int kz = 1; kz < n; ++kz, zb.next()) {
+    load_lplane(up, lab, kx, ky, kz, n, nm1);
+    const int o = W2 * kz;
+    const T pv = p[o];
+    d[o] += al * pv;
+    const T rv = r[o] - al * q[o] - ctt_node(vec, lo, up, bxy, zb.lo, zb.up, nq);
+    r[o] = rv;
+    if (!last) p[o] = mi[o] * rv + be * pv;
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) lo[i][j] = up[i][j];
+  }
 }
 
 template <typename T>
 struct Col {
   int u, slot, pt, kx, ky;
+  int bxy[4];  // sub-block index (within a z-block) of the element columns c = 2 sy + sx
 };
 
 template <typename T>
@@ -253,19 +364,28 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
     cl.kx = 1 + t % ni;
     cl.ky = 1 + t / ni;
     cl.pt = cl.u / R;
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+      cl.bxy[c] = ((cl.ky - 1 + (c >> 1)) / m) * P + (cl.kx - 1 + (c & 1)) / m;
   };
-  // S^-1 v per slot (FP64 rows read column-wise: S^-1 is symmetric); v from `src`
-  // ([slot][nc] with stride), result in S.vec.
-  auto small_solve64 = [&](int s, const double *src, double sign, const double *gsub) {
-    const int pt = (u0 + s) / R;
-    const double *Si = a.Sinv64 + (size_t)pt * nc * nc;
-    for (int i = tid; i < nc; i += L3_THREADS) {
+  // lambda = S^-1 v for every active slot at once, one (slot, row) pair per thread (FP64; S^-1
+  // is symmetric, so its rows are read column-wise, coalesced across rows). v = the slot's
+  // constraint functionals of the previous phase, or g - those when with_g.
+  auto small_solve64_all = [&](bool with_g) {
+    const double *rb = rbuf();
+    for (int i = tid; i < K * nc; i += L3_THREADS) {
+      const int s = i / nc, row = i - s * nc;
+      if (S.flags[s] & F_DONE) continue;
+      const int u = u0 + s, pt = u / R;
+      const double *src = rb + (size_t)u * NACC + NACC_S;
+      const double *Si = a.Sinv64 + (size_t)pt * nc * nc;
+      const double *gs = with_g ? a.g + (size_t)pt * nc * R + u % R : nullptr;
       double acc = 0.0;
       for (int j = 0; j < nc; ++j) {
-        const double cj = gsub ? gsub[(size_t)j * R] - src[j] : sign * src[j];
-        acc += Si[(size_t)j * nc + i] * cj;
+        const double cj = gs ? gs[(size_t)j * R] - src[j] : src[j];
+        acc += Si[(size_t)j * nc + row] * cj;
       }
-      S.vec[s * nc + i] = acc;
+      S.vec[s * nc + row] = acc;
     }
   };
 
@@ -283,10 +403,12 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
       const size_t ub = (size_t)cl.u * a.nv + cl.kx + (size_t)W * cl.ky;
       const uint8_t *lab = a.labels + (size_t)cl.pt * n * n * n;
       ColBins<double> cb;
-      cb.init(S.bins + cl.slot * 2 * nc, cl.kx, cl.ky, m, P, nq);
+      cb.init(S.bins + cl.slot * 2 * nc, cl.bxy, nq);
       int lo[2][2], up[2][2];
       load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
-      for (int kz = 1; kz < n; ++kz) {
+      ZBlk zb;
+      zb.init(m, P * P);
+      for (int kz = 1; kz < n; ++kz, zb.next()) {
         load_lplane(up, lab, cl.kx, cl.ky, kz, n, a.N - 1);
         const size_t o = ub + W2 * kz;
         double xv = a.x[o];
@@ -296,9 +418,9 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
           a.d[o] = T(0);
         }
         cb.add(lo, xv);
-        if (kz % m == 0) {
+        if (zb.boundary()) {
           cb.flush();
-          cb.zb = kz / m;
+          cb.zoff = zb.up;
         }
         cb.add(up, xv);
 #pragma unroll
@@ -314,14 +436,7 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
 
     // ---- F2: mu = S^-1 (g - Ct x); x += M^-1 Ct^T mu
     clear_next();
-    {
-      const double *rb = rbuf();
-      for (int s = 0; s < K; ++s) {
-        if (S.flags[s] & F_DONE) continue;
-        const int u = u0 + s, pt = u / R, rf = u % R;
-        small_solve64(s, rb + (size_t)u * NACC + NACC_S, 1.0, a.g + (size_t)pt * nc * R + rf);
-      }
-    }
+    small_solve64_all(true);
     __syncthreads();
     for (long long c = c0 + tid; c < c1; c += L3_THREADS) {
       Col<T> cl;
@@ -333,10 +448,12 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
       const double *vec = S.vec + cl.slot * nc;
       int lo[2][2], up[2][2];
       load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
-      for (int kz = 1; kz < n; ++kz) {
+      ZBlk zb;
+      zb.init(m, P * P);
+      for (int kz = 1; kz < n; ++kz, zb.next()) {
         load_lplane(up, lab, cl.kx, cl.ky, kz, n, a.N - 1);
         const size_t o = ub + W2 * kz;
-        a.x[o] += a.minv64[mb + W2 * kz] * ctt_node(vec, lo, up, cl.kx, cl.ky, kz, m, P, nq);
+        a.x[o] += a.minv64[mb + W2 * kz] * ctt_node(vec, lo, up, cl.bxy, zb.lo, zb.up, nq);
 #pragma unroll
         for (int i = 0; i < 2; ++i)
 #pragma unroll
@@ -365,8 +482,10 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
       int lo[2][2], up[2][2];
       load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
       ColBins<double> cb;
-      cb.init(S.bins + cl.slot * 2 * nc, cl.kx, cl.ky, m, P, nq);
-      for (int kz = 1; kz < n; ++kz) {
+      cb.init(S.bins + cl.slot * 2 * nc, cl.bxy, nq);
+      ZBlk zb;
+      zb.init(m, P * P);
+      for (int kz = 1; kz < n; ++kz, zb.next()) {
         load_plane9(v[2], a.x, ub + W2 * (kz + 1), W);
         load_kplane(k[1], kap, cl.kx, cl.ky, kz, n);
         load_lplane(up, lab, cl.kx, cl.ky, kz, n, a.N - 1);
@@ -376,9 +495,9 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
         a.r64[o] = r;
         const double mr = a.minv64[mb + W2 * kz] * r;
         cb.add(lo, mr);
-        if (kz % m == 0) {
+        if (zb.boundary()) {
           cb.flush();
-          cb.zb = kz / m;
+          cb.zoff = zb.up;
         }
         cb.add(up, mr);
 #pragma unroll
@@ -405,14 +524,7 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
     // ---- F4: lambda = S^-1 Ct M^-1 r; r -= Ct^T lambda; rho64; inner vectors
     clear_next();
     zero_local();
-    {
-      const double *rb = rbuf();
-      for (int s = 0; s < K; ++s) {
-        if (S.flags[s] & F_DONE) continue;
-        const int u = u0 + s;
-        small_solve64(s, rb + (size_t)u * NACC + NACC_S, 1.0, nullptr);
-      }
-    }
+    small_solve64_all(false);
     __syncthreads();
     for (int s = 0; s < K; ++s) {
       const int u = u0 + s;
@@ -430,10 +542,12 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
       int lo[2][2], up[2][2];
       load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
       double rho = 0.0;
-      for (int kz = 1; kz < n; ++kz) {
+      ZBlk zb;
+      zb.init(m, P * P);
+      for (int kz = 1; kz < n; ++kz, zb.next()) {
         load_lplane(up, lab, cl.kx, cl.ky, kz, n, a.N - 1);
         const size_t o = ub + W2 * kz;
-        const double r = a.r64[o] - ctt_node(vec, lo, up, cl.kx, cl.ky, kz, m, P, nq);
+        const double r = a.r64[o] - ctt_node(vec, lo, up, cl.bxy, zb.lo, zb.up, nq);
         const double mi = a.minv64[mb + W2 * kz];
         rho += r * mi * r;
         const T rt = (T)r;
@@ -489,61 +603,37 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
         if (!(S.flags[cl.slot] & F_INNER)) continue;
         const size_t ub = (size_t)cl.u * a.nv + cl.kx + (size_t)W * cl.ky;
         const size_t mb = (size_t)cl.pt * a.nv + cl.kx + (size_t)W * cl.ky;
-        const uint8_t *lab = a.labels + (size_t)cl.pt * n * n * n;
-        const T *kap = a.kapT + (size_t)cl.pt * n * n * n;
-        T v[3][3][3], k[2][2][2];
-        load_plane9(v[0], a.p, ub, W);
-        load_plane9(v[1], a.p, ub + W2, W);
-        load_kplane(k[0], kap, cl.kx, cl.ky, 0, n);
-        int lo[2][2], up[2][2];
-        load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
         ColBins<T> bz, bq;
         double *sb = S.bins + cl.slot * 2 * nc;
-        bz.init(sb, cl.kx, cl.ky, m, P, nq);
-        bq.init(sb + nc, cl.kx, cl.ky, m, P, nq);
-        T pq = 0, zq = 0, qmq = 0, rz = 0;
-        const T hT = (T)a.h;
-        for (int kz = 1; kz < n; ++kz) {
-          load_plane9(v[2], a.p, ub + W2 * (kz + 1), W);
-          load_kplane(k[1], kap, cl.kx, cl.ky, kz, n);
-          load_lplane(up, lab, cl.kx, cl.ky, kz, n, a.N - 1);
-          const size_t o = ub + W2 * kz;
-          const T q = hT * q1_apply3d<T>(v, k);
-          a.q[o] = q;
-          const T mi = a.minvT[mb + W2 * kz];
-          const T r = a.r[o];
-          const T z = mi * r, qm = mi * q;
-          pq += v[1][1][1] * q;
-          zq += z * q;
-          qmq += q * qm;
-          rz += r * z;
-          bz.add(lo, z);
-          bq.add(lo, qm);
-          if (kz % m == 0) {
-            bz.flush();
-            bq.flush();
-            bz.zb = bq.zb = kz / m;
-          }
-          bz.add(up, z);
-          bq.add(up, qm);
-#pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-              v[0][i][j] = v[1][i][j];
-              v[1][i][j] = v[2][i][j];
-            }
-#pragma unroll
-          for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) {
-              k[0][i][j] = k[1][i][j];
-              lo[i][j] = up[i][j];
-            }
-        }
-        bz.flush();
-        bq.flush();
+        bz.init(sb, cl.bxy, nq);
+        bq.init(sb + nc, cl.bxy, nq);
+        T sum[4] = {0, 0, 0, 0};
+        p1_column<T>(a.p + ub, a.q + ub, a.r + ub, a.minvT + mb,
+                     a.kapT + (size_t)cl.pt * n * n * n, a.labels + (size_t)cl.pt * n * n * n, n,
+                     cl.kx, cl.ky, m, P * P, a.N - 1, (T)a.h, bz, bq, sum);
+        const T pq = sum[0], zq = sum[1], qmq = sum[2], rz = sum[3];
         double *ss = S.sums + cl.slot * 8;
+        {
+          // one atomic per warp when all its lanes walk columns of the same unit
+          const unsigned act = __activemask();
+          if (act == 0xffffffffu && __match_any_sync(act, cl.slot) == act) {
+            double w0 = pq, w1 = zq, w2 = qmq, w3 = rz;
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+              w0 += __shfl_xor_sync(act, w0, o);
+              w1 += __shfl_xor_sync(act, w1, o);
+              w2 += __shfl_xor_sync(act, w2, o);
+              w3 += __shfl_xor_sync(act, w3, o);
+            }
+            if ((tid & 31) == 0) {
+              atomicAdd(&ss[0], w0);
+              atomicAdd(&ss[1], w1);
+              atomicAdd(&ss[2], w2);
+              atomicAdd(&ss[3], w3);
+            }
+            continue;
+          }
+        }
         atomicAdd(&ss[0], (double)pq);
         atomicAdd(&ss[1], (double)zq);
         atomicAdd(&ss[2], (double)qmq);
@@ -557,30 +647,43 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
         break;
       }
 
-      // ---- P2: scalars, lambda, updates
+      // ---- P2: scalars, lambda, updates (all slots of the CTA at once)
       clear_next();
       {
         const double *rb = rbuf();
-        for (int s = 0; s < K; ++s) {
+        // c = Ct z - alpha Ct M^-1 q into the first half of the slot's bins
+        for (int i = tid; i < K * nc; i += L3_THREADS) {
+          const int s = i / nc, j = i - s * nc;
           if (!(S.flags[s] & F_INNER)) continue;
-          const int u = u0 + s, pt = u / R;
-          const double *acc = rb + (size_t)u * NACC;
+          const double *acc = rb + (size_t)(u0 + s) * NACC;
           const double alpha = S.rho[s] / acc[0];
-          // c = Ct z - alpha Ct M^-1 q into the shared bins of the slot, lambda = S^-1 c
-          for (int i = tid; i < nc; i += L3_THREADS)
-            S.bins[s * 2 * nc + i] = acc[NACC_S + i] - alpha * acc[NACC_S + nc + i];
-          __syncthreads();
-          const T *Si = a.SinvT + (size_t)pt * nc * nc;
-          for (int i = tid; i < nc; i += L3_THREADS) {
-            T l = 0;
-            for (int j = 0; j < nc; ++j) l += Si[(size_t)j * nc + i] * (T)S.bins[s * 2 * nc + j];
-            S.vec[s * nc + i] = (double)l;
-            vecT(s)[i] = l;
-          }
-          __syncthreads();
-          if (tid == 0) {
-            double lc = 0.0;
-            for (int i = 0; i < nc; ++i) lc += S.vec[s * nc + i] * S.bins[s * 2 * nc + i];
+          S.bins[s * 2 * nc + j] = acc[NACC_S + j] - alpha * acc[NACC_S + nc + j];
+        }
+        __syncthreads();
+        // lambda = S^-1 c in the inner precision, one (slot, row) pair per thread
+        for (int i = tid; i < K * nc; i += L3_THREADS) {
+          const int s = i / nc, row = i - s * nc;
+          if (!(S.flags[s] & F_INNER)) continue;
+          const T *Si = a.SinvT + (size_t)((u0 + s) / R) * nc * nc;
+          const double *cs = S.bins + s * 2 * nc;
+          T l = 0;
+          for (int j = 0; j < nc; ++j) l += Si[(size_t)j * nc + row] * (T)cs[j];
+          S.vec[s * nc + row] = (double)l;
+          vecT(s)[row] = l;
+        }
+        __syncthreads();
+        // scalars: one warp per slot (the same lane order in every CTA, so every CTA that
+        // holds a unit takes the same decisions)
+        const int lane = tid & 31;
+        for (int s = tid >> 5; s < K; s += L3_THREADS / 32) {
+          if (!(S.flags[s] & F_INNER)) continue;
+          double lc = 0.0;
+          for (int i = lane; i < nc; i += 32) lc += S.vec[s * nc + i] * S.bins[s * 2 * nc + i];
+#pragma unroll
+          for (int o = 16; o; o >>= 1) lc += __shfl_xor_sync(0xffffffffu, lc, o);
+          if (lane == 0) {
+            const double *acc = rb + (size_t)(u0 + s) * NACC;
+            const double alpha = S.rho[s] / acc[0];
             const double rn = acc[3] - 2.0 * alpha * acc[1] + alpha * alpha * acc[2] - lc;
             S.alpha[s] = alpha;
             S.beta[s] = rn / S.rho[s];
@@ -595,8 +698,8 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
                 S.flags[s] |= 8;  // last update of this sweep
             }
           }
-          __syncthreads();
         }
+        __syncthreads();
       }
       for (long long c = c0 + tid; c < c1; c += L3_THREADS) {
         Col<T> cl;
@@ -605,24 +708,10 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
         if (!(f & F_INNER)) continue;
         const size_t ub = (size_t)cl.u * a.nv + cl.kx + (size_t)W * cl.ky;
         const size_t mb = (size_t)cl.pt * a.nv + cl.kx + (size_t)W * cl.ky;
-        const uint8_t *lab = a.labels + (size_t)cl.pt * n * n * n;
-        const T *vec = vecT(cl.slot);
-        const T al = (T)S.alpha[cl.slot], be = (T)S.beta[cl.slot];
-        int lo[2][2], up[2][2];
-        load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
-        for (int kz = 1; kz < n; ++kz) {
-          load_lplane(up, lab, cl.kx, cl.ky, kz, n, a.N - 1);
-          const size_t o = ub + W2 * kz;
-          const T p = a.p[o];
-          a.d[o] += al * p;
-          const T r = a.r[o] - al * a.q[o] - ctt_node(vec, lo, up, cl.kx, cl.ky, kz, m, P, nq);
-          a.r[o] = r;
-          if (!(f & 8)) a.p[o] = a.minvT[mb + W2 * kz] * r + be * p;
-#pragma unroll
-          for (int i = 0; i < 2; ++i)
-#pragma unroll
-            for (int j = 0; j < 2; ++j) lo[i][j] = up[i][j];
-        }
+        p2_column<T>(a.d + ub, a.r + ub, a.p + ub, a.q + ub, a.minvT + mb,
+                     a.labels + (size_t)cl.pt * n * n * n, vecT(cl.slot), n, cl.kx, cl.ky, cl.bxy,
+                     m, P * P, nq, a.N - 1, (T)S.alpha[cl.slot], (T)S.beta[cl.slot],
+                     (f & 8) != 0);
       }
       __syncthreads();
       if (tid == 0) {
