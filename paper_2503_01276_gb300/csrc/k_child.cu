@@ -76,12 +76,11 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
   const V sixth = S::from(1.0 / 6.0);
   const typename S::P phv = S::vec(a.phi, unit, a.nvf), yv = S::vec(a.y, unit, a.nvf);
   const typename S::P yrv = a.yR ? S::vec(a.yR, unit, a.nvf) : nullptr;
-  // kappa of a level-n element in V (prepared planes avoid a conversion per node)
+  // kappa of a level-n element in V: float-float storage reads the prepared planes (a
+  // double -> float conversion runs on the FP64 pipe, about 1/100 of the FP32 rate here)
   auto kval = [&](int e) -> V {
-    if constexpr (std::is_same<V, ff>::value) {
-      if (a.kappa_ff) return ff_load(a.kappa_ff, pt, ncg * ncg, e);
-    }
-    return S::from(kc[e]);
+    if constexpr (std::is_same<V, ff>::value) return ff_load(a.kappa_ff, pt, ncg * ncg, e);
+    else return kc[e];
   };
   for (int t = tid; t < (row_hi - row_lo) * W; t += CF_THREADS) {
     const int row = row_lo + t / W, col = t % W;
@@ -284,7 +283,7 @@ __global__ void k_from_ff(const double *src, int nvs, double *dst, int nvd, int 
 }  // namespace
 
 cudaError_t launch_child_fine2d(const ChildArgs &a, bool ffs, cudaStream_t st) {
-  if (a.nf < 32 || a.nf > 256) return cudaErrorInvalidValue;
+  if (a.nf < 32 || a.nf > 256 || (ffs && !a.kappa_ff)) return cudaErrorInvalidValue;
   dim3 grid((a.nf + 1 + CF_BR - 1) / CF_BR, a.npts * a.R);
 #define CF_LAUNCH(NCV)                                                             \
   (ffs ? (k_child_fine2d<NCV, FFS><<<grid, CF_THREADS, 0, st>>>(a), 0)            \

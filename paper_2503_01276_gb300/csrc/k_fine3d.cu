@@ -98,13 +98,20 @@ template <class S>
 __global__ void __launch_bounds__(F3_THREADS) k_interp3d(ChildArgs a) {
   using V = typename S::V;
   const int unit = blockIdx.y, pt = unit / a.R, r = unit % a.R;
+  // the point's parent vectors and weights, converted once per block
+  __shared__ typename S::P pp[8];
+  __shared__ V pw[8];
+  if (threadIdx.x < a.slots) {
+    const double *b = a.par_ptr[pt * a.slots + threadIdx.x];
+    pp[threadIdx.x] = b ? S::vec(b, r, a.nvf) : nullptr;
+    pw[threadIdx.x] = S::from(a.par_w[pt * a.slots + threadIdx.x]);
+  }
+  __syncthreads();
   const int k = blockIdx.x * F3_THREADS + threadIdx.x;
   if (k >= a.nvf) return;
   V v = S::zero();
-  for (int s = 0; s < a.slots; ++s) {
-    const double *pp = a.par_ptr[pt * a.slots + s];
-    if (pp) v += S::from(a.par_w[pt * a.slots + s]) * S::ld(pp, r, a.nvf, k);
-  }
+  for (int s = 0; s < a.slots; ++s)
+    if (pp[s]) v += pw[s] * S::ldv(pp[s], a.nvf, k);
   S::st(a.phi, unit, a.nvf, k, v);
 }
 
@@ -128,11 +135,11 @@ __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double
     const uint8_t *lc = a.labels_c + (size_t)pt * ncg * ncg * ncg;
     const size_t base = kx + (size_t)W * ky;
     const V third = S::from(1.0 / 3.0), twelfth = S::from(1.0 / 12.0), hv = S::from(hf);
+    // float-float storage reads the prepared kappa planes (no conversion per node)
     auto kval = [&](size_t c) -> V {
-      if constexpr (std::is_same<V, ff>::value) {
-        if (a.kappa_ff) return ff_load(a.kappa_ff, pt, ncg * ncg * ncg, (int)c);
-      }
-      return S::from(kc[c]);
+      if constexpr (std::is_same<V, ff>::value)
+        return ff_load(a.kappa_ff, pt, ncg * ncg * ncg, (int)c);
+      else return kc[c];
     };
     V v[3][3][3], kk[2][2][2];
     int lo[2][2], up[2][2];
@@ -431,6 +438,7 @@ cudaError_t launch_apply3d(const ApplyArgs &a, double h, cudaStream_t st) {
 }
 
 cudaError_t launch_interp3d(const ChildArgs &a, cudaStream_t st, bool ffs) {
+  if (a.slots > 8) return cudaErrorInvalidValue;
   dim3 grid((a.nvf + F3_THREADS - 1) / F3_THREADS, a.npts * a.R);
   if (ffs) k_interp3d<FFS><<<grid, F3_THREADS, 0, st>>>(a);
   else k_interp3d<F64S><<<grid, F3_THREADS, 0, st>>>(a);
@@ -438,7 +446,7 @@ cudaError_t launch_interp3d(const ChildArgs &a, cudaStream_t st, bool ffs) {
 }
 
 cudaError_t launch_fine_apply3d(const ChildArgs &a, double hf, cudaStream_t st, bool ffs) {
-  if (a.nc > MCH_MAX_NC3) return cudaErrorInvalidValue;
+  if (a.nc > MCH_MAX_NC3 || (ffs && !a.kappa_ff)) return cudaErrorInvalidValue;
   const int ni = a.nf - 1;
   dim3 grid((ni * ni + F3_THREADS - 1) / F3_THREADS, a.npts * a.R);
   if (ffs) {
