@@ -11,8 +11,10 @@
 //   two_prod      exact product with one FMA: p + e == a * b exactly.
 // Word operations follow the double-word algorithms of Joldes, Muller and Popescu
 // ("Tight and rigorous error bounds for basic building blocks of double-word arithmetic",
-// ACM TOMS 2017): the accurate sum of two double-words (relative error <= 3u^2) and the
-// product with one or two FMAs (relative error <= 5u^2 / 4u^2), u = 2^-24.
+// ACM TOMS 2017), u = 2^-24: the sum is their "sloppy" double-word sum (one two_sum on the
+// high words; absolute error about 2u^2 (|a| + |b|), i.e. bounded like an FP64 sum's by the
+// operands' size rather than the result's, which is all the stencils, interpolations and
+// reductions here need), the products use one or two FMAs (relative error <= 5u^2 / 4u^2).
 //
 // Storage: a vector of nv entries occupies the space of nv doubles as a hi plane [nv] followed
 // by a lo plane [nv].
@@ -46,12 +48,9 @@ __device__ __forceinline__ double ff_to(ff a) { return (double)a.h + (double)a.l
 __device__ __forceinline__ ff ff_of(float f) { return ff{f, 0.f}; }
 
 __device__ __forceinline__ ff operator+(ff a, ff b) {
-  float s, e, t, f;
+  float s, e;
   two_sum(a.h, b.h, s, e);
-  two_sum(a.l, b.l, t, f);
-  e = __fadd_rn(e, t);
-  fast_two_sum(s, e, s, e);
-  e = __fadd_rn(e, f);
+  e = __fadd_rn(e, __fadd_rn(a.l, b.l));
   fast_two_sum(s, e, s, e);
   return ff{s, e};
 }
@@ -78,14 +77,8 @@ __device__ __forceinline__ ff operator*(float b, ff a) { return a * b; }
 __device__ __forceinline__ ff &operator+=(ff &a, ff b) { return a = a + b; }
 __device__ __forceinline__ ff &operator-=(ff &a, ff b) { return a = a - b; }
 
-// acc += p with one two_sum on the high words (the cheaper "sloppy" double-word sum): error a
-// few units of 2^-47 of |acc| + |p|, enough for long reductions of mostly same-sign terms.
-__device__ __forceinline__ void ff_acc(ff &acc, ff p) {
-  float s, e;
-  two_sum(acc.h, p.h, s, e);
-  e = __fadd_rn(e, __fadd_rn(acc.l, p.l));
-  fast_two_sum(s, e, acc.h, acc.l);
-}
+// acc += p
+__device__ __forceinline__ void ff_acc(ff &acc, ff p) { acc = acc + p; }
 
 // plane access: vector v (index of a whole vector) of a batch with stride nv entries
 __device__ __forceinline__ ff ff_load(const double *base, size_t v, int nv, int k) {
