@@ -72,8 +72,16 @@ __device__ __forceinline__ void load_kplane(V (&k)[2][2], const V *kap, int kx, 
       k[sy][sx] = kap[(kx - 1 + sx) + (size_t)n * ((ky - 1 + sy) + (size_t)n * ez)];
 }
 
-// labels >= N (invalid input, reported by the setup) are clamped so that no row index leaves
-// the multiplier tables
+// Labels of the four elements of element plane ez around node column (kx, ky), one byte per
+// element column c = 2 sy + sx. Labels >= N (invalid input, reported by the setup) are
+// clamped so that no row index leaves the multiplier tables; N <= 128 keeps the key >= 0.
+__device__ __forceinline__ int lkey(const uint8_t *lab, int kx, int ky, int ez, int n, int nm1) {
+  const uint8_t *l = lab + (kx - 1) + (size_t)n * ((ky - 1) + (size_t)n * ez);
+  return min((int)l[0], nm1) | (min((int)l[1], nm1) << 8) | (min((int)l[n], nm1) << 16) |
+         (min((int)l[n + 1], nm1) << 24);
+}
+
+// The same four labels (clamped likewise) as l[sy][sx].
 __device__ __forceinline__ void load_lplane(int (&l)[2][2], const uint8_t *lab, int kx, int ky,
                                             int ez, int n, int nm1) {
 #pragma unroll
@@ -83,10 +91,6 @@ __device__ __forceinline__ void load_lplane(int (&l)[2][2], const uint8_t *lab, 
       l[sy][sx] = min((int)lab[(kx - 1 + sx) + (size_t)n * ((ky - 1 + sy) + (size_t)n * ez)], nm1);
 }
 
-// Per-column accumulation of node values into the constraint rows of the adjacent elements
-// (node-based form of Ct v): each of the four element columns (sx, sy) around the node column
-// keeps one partial sum for its current label and z-block; a change of label or of z-block
-// flushes it to shared memory (labels change rarely along a column).
 // Sub-block offsets along a node column, advanced without divisions: for node kz, lo and up
 // are (z-block of the element plane below, resp. above) * P^2, and boundary() says that kz is
 // a multiple of m (the two planes lie in different z-blocks).
@@ -155,21 +159,45 @@ struct ColBins {
   }
 };
 
-// Ct^T vec at a node from the labels of its 8 adjacent elements (lower plane ez = kz-1 in the
-// z-block at offset zlo, upper plane ez = kz at zup).
+// Ct^T vec restricted to one element plane: the multipliers of its four elements' rows.
 template <typename V>
-__device__ __forceinline__ V ctt_node(const V *vec, const int (&lo)[2][2], const int (&up)[2][2],
-                                      const int (&bxy)[4], int zlo, int zup, int nq) {
-  V s = 0;
-#pragma unroll
-  for (int c = 0; c < 4; ++c)
-    s += vec[lo[c >> 1][c & 1] * nq + zlo + bxy[c]] + vec[up[c >> 1][c & 1] * nq + zup + bxy[c]];
-  return s;
+__device__ __forceinline__ V plane_ctt(const V *vec, int key, int zoff, const int (&bxy)[4],
+                                       int nq) {
+  return (vec[(key & 255) * nq + zoff + bxy[0]] + vec[((key >> 8) & 255) * nq + zoff + bxy[1]]) +
+         (vec[((key >> 16) & 255) * nq + zoff + bxy[2]] +
+          vec[((key >> 24) & 255) * nq + zoff + bxy[3]]);
 }
 
-// The two passes of an inner iteration over one node column (kz = 1..n-1) of a unit. The
-// vectors are passed as restrict-qualified pointers to the column's base so that the loads of
-// the next z step may be issued ahead of the stores of the current one.
+// Ct^T vec along a node column: the value at node kz is the sum of the plane sums below and
+// above; the plane below is the previous node's plane above, and a plane sum is recomputed
+// only when its labels or z-block change.
+template <typename V>
+struct ColCtt {
+  V below, above;
+  int key, zoff;
+  // node 1: planes 0 and 1
+  __device__ __forceinline__ void init(const V *vec, int key0, int key1, const ZBlk &zb,
+                                       const int (&bxy)[4], int nq) {
+    below = plane_ctt(vec, key0, zb.lo, bxy, nq);
+    above = plane_ctt(vec, key1, zb.up, bxy, nq);
+    key = key1;
+    zoff = zb.up;
+  }
+  // moves to the next node, whose plane above has labels key_up and offset zup
+  __device__ __forceinline__ void next(const V *vec, int key_up, int zup, const int (&bxy)[4],
+                                       int nq) {
+    below = above;
+    if (key_up != key || zup != zoff) {
+      above = plane_ctt(vec, key_up, zup, bxy, nq);
+      key = key_up;
+      zoff = zup;
+    }
+  }
+  __device__ __forceinline__ V value() const { return below + above; }
+};
+
+// The two passes of an inner iteration over one node column (kz = 1..n-1) of a unit, with the
+// vectors passed as restrict-qualified pointers to the column's base.
 
 // q = h A p; the column's sums p.q, z.q, q.M^-1 q, r.z (z = M^-1 r) and its constraint
 // functionals Ct z, Ct M^-1 q into the bins.
@@ -230,7 +258,9 @@ __device__ __forceinline__ void p1_column(const T *__restrict__ p, T *__restrict
   bq.flush();
 }
 
-// delta += alpha p; r <- r - alpha q - Ct^T lambda; p = M^-1 r + beta p (unless last)
+// delta += alpha p; r <- r - alpha q - Ct^T lambda; p = M^-1 r + beta p (unless last).
+// Software-pipelined: node kz+1's operands are loaded before node kz is computed, so that
+// two z steps of loads are in flight.
 template <typename T>
 __device__ __forceinline__ void p2_column(T *__restrict__ d, T *__restrict__ r,
                                           T *__restrict__ p, const T *__restrict__ q,
@@ -240,23 +270,39 @@ __device__ __forceinline__ void p2_column(T *__restrict__ d, T *__restrict__ r,
                                           const int (&bxy)[4], int m, int pp, int nq, int nm1,
                                           T al, T be, bool last) {
   const int W = n + 1, W2 = W * W;
-  int lo[2][2], up[2][2];
-  load_lplane(lo, lab, kx, ky, 0, n, nm1);
   ZBlk zb;
   zb.init(m, pp);
-#pragma unroll 4
-  for (int kz = 1; kz < n; ++kz, zb.next()) {
-    load_lplane(up, lab, kx, ky, kz, n, nm1);
-    const int o = W2 * kz;
-    const T pv = p[o];
-    d[o] += al * pv;
-    const T rv = r[o] - al * q[o] - ctt_node(vec, lo, up, bxy, zb.lo, zb.up, nq);
-    r[o] = rv;
-    if (!last) p[o] = mi[o] * rv + be * pv;
-#pragma unroll
-    for (int i = 0; i < 2; ++i)
-#pragma unroll
-      for (int j = 0; j < 2; ++j) lo[i][j] = up[i][j];
+  ColCtt<T> ct;
+  ct.init(vec, lkey(lab, kx, ky, 0, n, nm1), lkey(lab, kx, ky, 1, n, nm1), zb, bxy, nq);
+  int o = W2;
+  T pv = p[o], dv = d[o], rv = r[o], qv = q[o], mv = mi[o];
+  for (int kz = 1; kz < n; ++kz) {
+    const int on = o + W2;
+    const bool more = kz + 1 < n;
+    T pn = 0, dn = 0, rn = 0, qn = 0, mn = 0;
+    int kn = 0;
+    if (more) {
+      pn = p[on];
+      dn = d[on];
+      rn = r[on];
+      qn = q[on];
+      mn = mi[on];
+      kn = lkey(lab, kx, ky, kz + 1, n, nm1);
+    }
+    d[o] = dv + al * pv;
+    const T rr = rv - al * qv - ct.value();
+    r[o] = rr;
+    if (!last) p[o] = mv * rr + be * pv;
+    if (more) {
+      zb.next();
+      ct.next(vec, kn, zb.up, bxy, nq);
+    }
+    o = on;
+    pv = pn;
+    dv = dn;
+    rv = rn;
+    qv = qn;
+    mv = mn;
   }
 }
 
@@ -446,18 +492,18 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
       const size_t mb = (size_t)cl.pt * a.nv + cl.kx + (size_t)W * cl.ky;
       const uint8_t *lab = a.labels + (size_t)cl.pt * n * n * n;
       const double *vec = S.vec + cl.slot * nc;
-      int lo[2][2], up[2][2];
-      load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
       ZBlk zb;
       zb.init(m, P * P);
-      for (int kz = 1; kz < n; ++kz, zb.next()) {
-        load_lplane(up, lab, cl.kx, cl.ky, kz, n, a.N - 1);
+      ColCtt<double> ct;
+      ct.init(vec, lkey(lab, cl.kx, cl.ky, 0, n, a.N - 1), lkey(lab, cl.kx, cl.ky, 1, n, a.N - 1),
+              zb, cl.bxy, nq);
+      for (int kz = 1; kz < n; ++kz) {
         const size_t o = ub + W2 * kz;
-        a.x[o] += a.minv64[mb + W2 * kz] * ctt_node(vec, lo, up, cl.bxy, zb.lo, zb.up, nq);
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-          for (int j = 0; j < 2; ++j) lo[i][j] = up[i][j];
+        a.x[o] += a.minv64[mb + W2 * kz] * ct.value();
+        if (kz + 1 < n) {
+          zb.next();
+          ct.next(vec, lkey(lab, cl.kx, cl.ky, kz + 1, n, a.N - 1), zb.up, cl.bxy, nq);
+        }
       }
     }
     sync();
@@ -539,24 +585,24 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
       const size_t mb = (size_t)cl.pt * a.nv + cl.kx + (size_t)W * cl.ky;
       const uint8_t *lab = a.labels + (size_t)cl.pt * n * n * n;
       const double *vec = S.vec + cl.slot * nc;
-      int lo[2][2], up[2][2];
-      load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
       double rho = 0.0;
       ZBlk zb;
       zb.init(m, P * P);
-      for (int kz = 1; kz < n; ++kz, zb.next()) {
-        load_lplane(up, lab, cl.kx, cl.ky, kz, n, a.N - 1);
+      ColCtt<double> ct;
+      ct.init(vec, lkey(lab, cl.kx, cl.ky, 0, n, a.N - 1), lkey(lab, cl.kx, cl.ky, 1, n, a.N - 1),
+              zb, cl.bxy, nq);
+      for (int kz = 1; kz < n; ++kz) {
         const size_t o = ub + W2 * kz;
-        const double r = a.r64[o] - ctt_node(vec, lo, up, cl.bxy, zb.lo, zb.up, nq);
+        const double r = a.r64[o] - ct.value();
         const double mi = a.minv64[mb + W2 * kz];
         rho += r * mi * r;
         const T rt = (T)r;
         a.r[o] = rt;
         a.p[o] = a.minvT[mb + W2 * kz] * rt;
-#pragma unroll
-        for (int i = 0; i < 2; ++i)
-#pragma unroll
-          for (int j = 0; j < 2; ++j) lo[i][j] = up[i][j];
+        if (kz + 1 < n) {
+          zb.next();
+          ct.next(vec, lkey(lab, cl.kx, cl.ky, kz + 1, n, a.N - 1), zb.up, cl.bxy, nq);
+        }
       }
       atomicAdd(&S.sums[cl.slot * 8 + 4], rho);
     }
