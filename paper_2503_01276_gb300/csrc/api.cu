@@ -639,8 +639,9 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
       ++h->launches;
     }
     CK(launch_child(h, L, L.gI, &nl), "child fine");
+    // K_I = I^T A_1 I (or with A_1 restricted to R_p): a symmetric form
     CK(launch_gram((int)np, R, L.nvf, L.phi, ovs ? h->yfineR : h->yfine, inv_vol, L.E, st,
-                   h->ffs),
+                   h->ffs, true),
        "gram I");
     CK(launch_restrict(h, L, h->yfine, -1.0, L.b, h->ffs), "restrict");
     if (ovs) {

@@ -162,7 +162,9 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
 
 constexpr int GR_THREADS = 256;
 
-template <int R, class S>
+// E += alpha sym(X^T Y) per point (R vectors each). SYM: Y is the image of X under a
+// symmetric operator (Y = A_1 X), so X^T Y is symmetric and one product per pair suffices.
+template <int R, class S, bool SYM>
 __global__ void __launch_bounds__(GR_THREADS) k_gram2d(int nv, int slices, const double *X,
                                                         const double *Y, double alpha, double *E) {
   using V = typename S::V;
@@ -187,7 +189,10 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram2d(int nv, int slices, const
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
-      for (int s = r; s < R; ++s, ++p) S::acc2(acc[p], xv[r], yv[s], yv[r], xv[s]);
+      for (int s = r; s < R; ++s, ++p) {
+        if constexpr (SYM) acc[p] = acc[p] + xv[r] * yv[s];
+        else S::acc2(acc[p], xv[r], yv[s], yv[r], xv[s]);
+      }
   }
   __shared__ double red[GR_THREADS / 32][NP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -204,7 +209,7 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram2d(int nv, int slices, const
     while (q >= R - rr) { q -= R - rr; ++rr; }
     cc = rr + q;
     double *Ep = E + (size_t)pt * R * R;
-    const double v = 0.5 * alpha * s;
+    const double v = (SYM ? 1.0 : 0.5) * alpha * s;
     atomicAdd(&Ep[rr * R + cc], v);
     if (cc != rr) atomicAdd(&Ep[cc * R + rr], v);
   }
@@ -295,7 +300,7 @@ cudaError_t launch_child_fine2d(const ChildArgs &a, bool ffs, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <class S>
+template <class S, bool SYM>
 cudaError_t gram_s(int npts, int R, int nv, const double *X, const double *Y, double alpha,
                    double *E, cudaStream_t st) {
   int slices = nv >= 8192 ? 8 : (nv >= 2048 ? 4 : 1);
@@ -306,21 +311,24 @@ cudaError_t gram_s(int npts, int R, int nv, const double *X, const double *Y, do
   }
   dim3 grid(npts, slices);
   switch (R) {
-    case 3: k_gram2d<3, S><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
-    case 4: k_gram2d<4, S><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
-    case 6: k_gram2d<6, S><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
-    case 8: k_gram2d<8, S><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
-    case 9: k_gram2d<9, S><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
-    case 12: k_gram2d<12, S><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+    case 3: k_gram2d<3, S, SYM><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+    case 4: k_gram2d<4, S, SYM><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+    case 6: k_gram2d<6, S, SYM><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+    case 8: k_gram2d<8, S, SYM><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+    case 9: k_gram2d<9, S, SYM><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+    case 12: k_gram2d<12, S, SYM><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
 
 cudaError_t launch_gram(int npts, int R, int nv, const double *X, const double *Y,
-                        double alpha, double *E, cudaStream_t st, bool ffs) {
-  return ffs ? gram_s<FFS>(npts, R, nv, X, Y, alpha, E, st)
-             : gram_s<F64S>(npts, R, nv, X, Y, alpha, E, st);
+                        double alpha, double *E, cudaStream_t st, bool ffs, bool sym) {
+  if (sym)
+    return ffs ? gram_s<FFS, true>(npts, R, nv, X, Y, alpha, E, st)
+               : gram_s<F64S, true>(npts, R, nv, X, Y, alpha, E, st);
+  return ffs ? gram_s<FFS, false>(npts, R, nv, X, Y, alpha, E, st)
+             : gram_s<F64S, false>(npts, R, nv, X, Y, alpha, E, st);
 }
 
 template <class S>

@@ -63,9 +63,15 @@ __global__ void __launch_bounds__(SN_THREADS) k_setup_nodes(SetupArgs a, int sli
     }
     const int ex = e % n, ey = e / n;
     const int b = l * nq + (ey / m) * P + ex / m;
-    atomicAdd(&bsi[3 * b + 0], 1);
-    atomicAdd(&bsi[3 * b + 1], ex);
-    atomicAdd(&bsi[3 * b + 2], ey);
+    // lanes of the same bin add once (consecutive elements share a bin)
+    const unsigned peers = __match_any_sync(__activemask(), b);
+    const int cnt = __popc(peers);
+    const int sx = __reduce_add_sync(peers, ex), sy = __reduce_add_sync(peers, ey);
+    if ((tid & 31) == __ffs(peers) - 1) {
+      atomicAdd(&bsi[3 * b + 0], cnt);
+      atomicAdd(&bsi[3 * b + 1], sx);
+      atomicAdd(&bsi[3 * b + 2], sy);
+    }
   }
   __syncthreads();
   if (flags) {
@@ -114,7 +120,14 @@ __global__ void __launch_bounds__(SN_THREADS) k_setup_nodes(SetupArgs a, int sli
       }
       acc += dinv;
     }
-    flush();
+    // the column's last run: lanes with the same row signature add once
+    const unsigned peers = __match_any_sync(__activemask(), sig);
+    double tot = 0.0;
+    for (unsigned mm = peers; mm; mm &= mm - 1) tot += __shfl_sync(peers, acc, __ffs(mm) - 1);
+    if ((tid & 31) == __ffs(peers) - 1) {
+      acc = tot;
+      flush();
+    }
   }
   __syncthreads();
   double *Sg = a.Sacc + (size_t)pt * nc * nc;

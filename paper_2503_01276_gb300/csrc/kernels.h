@@ -118,9 +118,11 @@ struct ChildArgs {
 };
 cudaError_t launch_child_fine2d(const ChildArgs &a, bool ffs, cudaStream_t st);
 
-// E[pt][r][s] += alpha * 1/2 sum_k (X_r Y_s + Y_r X_s), R in {3, 4, 6, 8, 9, 12}.
+// E[pt][r][s] += alpha * 1/2 sum_k (X_r Y_s + Y_r X_s), R in {3, 4, 6, 8, 9, 12}; with sym
+// (Y = A X for a symmetric A, so the two terms agree) as alpha * sum_k X_r Y_s.
 cudaError_t launch_gram(int npts, int R, int nv, const double *X, const double *Y,
-                        double alpha, double *E, cudaStream_t st, bool ffs = false);
+                        double alpha, double *E, cudaStream_t st, bool ffs = false,
+                        bool sym = false);
 
 // ---------------------------------------------------------------------------------------
 // 3D (k3d.cuh conventions: (n+1)^3 lattice, nv = nv3_of(n))
