@@ -23,6 +23,9 @@ JSON line keys beyond the base contract:
                 copied in, effective coefficients copied out) inside the timed region.
   accuracy      largest final projected-residual ratio, and the block-relative error of
                 the sampled points against the oracle.
+  macro         the macroscopic problem (Eq. macro_eq) from the last step's coefficients,
+                outside the timed region: source densities of every level and the solve on
+                the coarse blocks, their CUDA-event times and the CG record.
 
 Multi-GPU (torchrun): every rank solves an independent hierarchy (a different medium
 seed, i.e. another macroscopic region) with no collective on the data path; weak scaling.
@@ -246,6 +249,31 @@ def _config(wl, precision):
             "l2": "flushed before every timed step (512 MB write, untimed)"}
 
 
+def macro_leg(s, wl, E_dev, stream):
+    """Source densities (mch_macro_source, the Gaussian source of Sec. 5: weights 1/contrast
+    and 1 for the two continua, alpha 40, centre of the unit domain) and the macroscopic solve
+    (mch_macro_solve) from device coefficients; times of each, the CG record and the size."""
+    import torch
+    d, N = wl.dim, wl.n_cont
+    w = np.ones(N)
+    w[0] = 1.0 / wl.contrast
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    fb = [torch.zeros((s.num_points(lev), N), dtype=torch.float64, device=E_dev[0].device)
+          for lev in range(1, wl.n_levels + 1)]
+    U = torch.zeros((N, (wl.macro_n + 1) ** d), dtype=torch.float64, device=E_dev[0].device)
+    ev[0].record(stream)
+    for lev in range(1, wl.n_levels + 1):
+        s.macro_source(lev, w, np.full(d, 0.5), 40.0, np.full(d, wl.origin), wl.spacing,
+                       out=fb[lev - 1])
+    ev[1].record(stream)
+    _, iters, rr = s.macro_solve(E_dev, fb, wl.spacing, tol=1e-12, out=U)
+    ev[2].record(stream)
+    torch.cuda.synchronize()
+    return {"source_ms": ev[0].elapsed_time(ev[1]), "solve_ms": ev[1].elapsed_time(ev[2]),
+            "cg_iters": iters, "relres": rr, "unknowns": int(N * (wl.macro_n - 1) ** d),
+            "max_abs_u": float(U.abs().max().item())}
+
+
 def plain_fp64_leg(wl, med_dev, flush, steps, stream):
     """The unbatched FP64 comparator: same workload and media, FP64 PCG, one macropoint per
     constrained-solve launch. Returns RHS/s, ms per step and the largest residual ratio."""
@@ -426,6 +454,10 @@ def main():
     d2h = sum(e.numel() * e.element_size() for e in E_host)
     e2e_value = whole_job_rate(rhs_per_step, world, e2e_steps, tt)
 
+    # the macroscopic problem (Sec. 2, Eq. macro_eq) from the last step's coefficients, outside
+    # the timed region: source densities of every level and the macro solve (CUDA events)
+    macro_info = macro_leg(s, wl, E_dev, stream)
+
     if rank != 0:
         if world > 1:
             dist.destroy_process_group()
@@ -499,7 +531,8 @@ def main():
             "e2e": {"value": e2e_value, "unit": "RHS/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": launches, "clocks": clocks,
-            "accuracy": {"max_relres": relres, "sampled_block_rel_err_vs_oracle": acc_err}}
+            "accuracy": {"max_relres": relres, "sampled_block_rel_err_vs_oracle": acc_err},
+            "macro": macro_info}
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

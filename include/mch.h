@@ -58,7 +58,7 @@ typedef enum {
 enum { MCH_FP64 = 0, MCH_MIXED = 1 };
 
 typedef struct {
-  int dim;                  /* d: 2 (3 is not built yet: MCH_ERR_UNSUPPORTED)               */
+  int dim;                  /* d: 2 or 3                                                    */
   int n_cont;               /* N: continua, 1..4                                            */
   int n_levels;             /* L                                                            */
   int eta;                  /* FE coarsening factor between levels (Sec. 3.2)               */
@@ -213,6 +213,36 @@ mch_status mch_autotune_level(mch_handle *h, int level, const double *kappa,
  * n = 1..L. Requires every level solved; with keep_parents = 0 the cell functions are
  * recomputed from the level-grid solutions first. */
 mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const *dL_dkappa);
+
+/* Source densities of the macroscopic problem (Sec. 2, Eq. Bs_defi, b_j / |K_p|, with the
+ * source of the numerical examples of Sec. 5) for every point of `level`:
+ *   fbar[p][j] = (1/|R_p|) int_{R_p} f phi_j,  j < N (the constant cell functions),
+ *   f(x) = weights[j] exp(-alpha |x - center|^2) in continuum j,
+ * f sampled at the centroids of the level-1-grid elements of the point's RVE at global
+ * positions x = x_p + y, x_p = origin + (macro index) * spacing (the element's continuum is
+ * that of the level-n element containing it); the integral is exact for this piecewise-
+ * constant f and the Q1 phi_j. weights [N], center [d], origin [d]: host memory. fbar
+ * [n_points][N] FP64, host or device. Requires the level solved; with keep_parents = 0 the
+ * cell functions are recomputed first. R_p follows mch_desc.overs. */
+mch_status mch_macro_source(mch_handle *h, int level, const double *weights,
+                            const double *center, double alpha, const double *origin,
+                            double spacing, double *fbar);
+
+/* Macroscopic multicontinuum solve (Sec. 2, Eq. macro_eq): the coarse blocks
+ * K_p = x_p + [-H/2, H/2]^d (H = spacing) of all macropoints form the macro mesh; U_j is Q1 on
+ * their (macro_n + 1)^d vertices (x fastest) with zero Dirichlet data on the outer boundary and
+ *   sum_p int_{K_p} w(V)^T E_p w(U) = sum_p int_{K_p} sum_j fbar_j(p) V_j,
+ * w(U) = (U_i, d_m U_i) in the order of the cell functions (r = i, r = N + i d + m), with E_p
+ * and fbar_p constant on K_p and integrated exactly (2 Gauss points per axis). E[n-1] points to
+ * [n_points][R][R] and fbar[n-1] to [n_points][N] of level n = 1..L (host or device; the
+ * outputs of mch_effective_coeffs and mch_macro_source). U: [N][(macro_n + 1)^d] FP64, host
+ * or device, boundary entries 0. FP64 Jacobi-PCG to ||r|| <= tol ||b|| (tol 0 -> 1e-12) in at
+ * most max_iter iterations (0 -> 20000); iters and relres (optional, host) receive the count
+ * and the final ||r|| / ||b||. MCH_ERR_NOT_CONVERGED if the tolerance is not met, and
+ * MCH_ERR_BREAKDOWN if the system is not positive definite (p'Ap <= 0). */
+mch_status mch_macro_solve(mch_handle *h, const double *const *E, const double *const *fbar,
+                           double spacing, double tol, int max_iter, double *U, int *iters,
+                           double *relres);
 
 /* Size of the fixed device buffer used by mch_direct_noalloc (32 MiB per GPU that loads the
  * library, held until the process exits). */

@@ -69,6 +69,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "mch_level_stats_get": (C.c_int, [P, C.c_int, C.POINTER(MchLevelStats)]),
         "mch_set_timing": (C.c_int, [P, C.c_int]),
         "mch_backward": (C.c_int, [P, P, P]),
+        "mch_macro_source": (C.c_int, [P, C.c_int, P, P, C.c_double, P, C.c_double, P]),
+        "mch_macro_solve": (C.c_int, [P, P, P, C.c_double, C.c_double, C.c_int, P,
+                                      C.POINTER(C.c_int), C.POINTER(C.c_double)]),
         "mch_direct_noalloc": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
                                          C.c_double, C.c_int, P, P, P, P]),
         "mch_destroy": (None, [P]),
@@ -263,6 +266,37 @@ class Solver:
         a = (P * self.n_levels)(*[_ptr(t) for t in dL_dE])
         b = (P * self.n_levels)(*[_ptr(t) for t in dL_dkappa])
         self._check(_LIB.mch_backward(self._h, a, b), "mch_backward")
+
+    def macro_source(self, level: int, weights, center, alpha: float, origin, spacing: float,
+                     out=None):
+        """Source densities fbar [points, N] of the macroscopic problem (mch_macro_source)."""
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        c = np.ascontiguousarray(center, dtype=np.float64)
+        o = np.ascontiguousarray(origin, dtype=np.float64)
+        if w.size != self.n_cont or c.size != self.dim or o.size != self.dim:
+            raise ValueError("weights need N entries, center and origin d entries")
+        if out is None:
+            out = np.zeros((self.num_points(level), self.n_cont))
+        self._check(_LIB.mch_macro_source(self._h, level, _ptr(w), _ptr(c), float(alpha),
+                                          _ptr(o), float(spacing), _ptr(out)),
+                    "mch_macro_source")
+        return out
+
+    def macro_solve(self, E, fbar, spacing: float, tol: float = 1e-12, max_iter: int = 0,
+                    out=None):
+        """Macroscopic solve (mch_macro_solve): E and fbar per level; returns
+        (U [N, (macro_n + 1)^d], iterations, relative residual)."""
+        P = C.c_void_p
+        a = (P * self.n_levels)(*[_ptr(t) for t in E])
+        b = (P * self.n_levels)(*[_ptr(t) for t in fbar])
+        if out is None:
+            out = np.zeros((self.n_cont, (self.desc.macro_n + 1) ** self.dim))
+        it = C.c_int(0)
+        rr = C.c_double(0.0)
+        self._check(_LIB.mch_macro_solve(self._h, a, b, float(spacing), float(tol), int(max_iter),
+                                         _ptr(out), C.byref(it), C.byref(rr)),
+                    "mch_macro_solve")
+        return out, it.value, rr.value
 
     def close(self):
         if self._h:

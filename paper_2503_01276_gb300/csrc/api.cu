@@ -850,6 +850,195 @@ mch_status mch_cell_functions(mch_handle *h, int level, double *phi) {
   return MCH_OK;
 }
 
+mch_status mch_macro_source(mch_handle *h, int level, const double *weights,
+                            const double *center, double alpha, const double *origin,
+                            double spacing, double *fbar) {
+  if (!valid_level(h, level) || !weights || !center || !origin || !fbar || !(spacing > 0.0) ||
+      !(alpha >= 0.0))
+    return set_err(h, MCH_ERR_ARG, "bad argument");
+  const mch_desc &d = h->d;
+  if (d.n_cont > MCH_MACRO_MAXN) return set_err(h, MCH_ERR_UNSUPPORTED, "at most 4 continua");
+  Level &L = h->lv[level - 1];
+  if (!L.solved) return set_err(h, MCH_ERR_ORDER, "level not solved");
+  CK(restore_phi(h), "recompute cell functions");
+  const int np = L.npts, N = d.n_cont, D = d.dim;
+  std::vector<double> xp((size_t)np * D);
+  for (int p = 0; p < np; ++p)
+    for (int a = 0; a < D; ++a)
+      xp[(size_t)p * D + a] = origin[a] + L.plan.points[(size_t)p * D + a] * spacing;
+  double *dxp = nullptr, *dout = nullptr;
+  CK(dalloc(h, &dxp, xp.size()), "positions");
+  CK(cudaMemcpyAsync(dxp, xp.data(), xp.size() * sizeof(double), cudaMemcpyHostToDevice, h->st),
+     "positions");
+  h->h2d += (long long)(xp.size() * sizeof(double));
+  const bool dev = is_device_ptr(fbar);
+  double *out = fbar;
+  if (!dev) {
+    CK(dalloc(h, &dout, (size_t)np * N), "source buffer");
+    out = dout;
+  }
+  MacroSourceArgs a{};
+  a.npts = np;
+  a.dim = D;
+  a.N = N;
+  a.R = h->R;
+  a.nf = d.n_fine;
+  a.lgr = ilog2(L.rho);
+  a.nvf = L.nvf;
+  a.P = d.periods;
+  a.overs = d.overs;
+  a.phi = L.phi;
+  a.labels = L.labels;
+  a.xp = dxp;
+  a.rve_len = d.rve_len;
+  a.alpha = alpha;
+  for (int j = 0; j < N; ++j) a.w[j] = weights[j];
+  for (int m = 0; m < D; ++m) a.c[m] = center[m];
+  a.fbar = out;
+  CK(launch_macro_source(a, h->ffs, h->st), "macro source");
+  ++h->launches;
+  if (!dev) {
+    CK(cudaMemcpyAsync(fbar, out, (size_t)np * N * sizeof(double), cudaMemcpyDeviceToHost,
+                       h->st),
+       "copy source");
+    h->d2h += (long long)((size_t)np * N * sizeof(double));
+  }
+  CK(cudaStreamSynchronize(h->st), "sync");
+  dfree(h, dxp);
+  dfree(h, dout);
+  return MCH_OK;
+}
+
+mch_status mch_macro_solve(mch_handle *h, const double *const *E, const double *const *fbar,
+                           double spacing, double tol, int max_iter, double *U, int *iters,
+                           double *relres) {
+  if (!h || !E || !fbar || !U || !(spacing > 0.0) || !(tol >= 0.0) || max_iter < 0)
+    return set_err(h, MCH_ERR_ARG, "bad argument");
+  const mch_desc &d = h->d;
+  const int D = d.dim, N = d.n_cont, R = h->R, M = d.macro_n;
+  if (N > MCH_MACRO_MAXN) return set_err(h, MCH_ERR_UNSUPPORTED, "at most 4 continua");
+  if (M < 2) return set_err(h, MCH_ERR_ARG, "macro grid too small");
+  if (tol == 0.0) tol = 1e-12;
+  if (max_iter == 0) max_iter = 20000;
+  size_t nel = 1, nn = 1;
+  for (int a = 0; a < D; ++a) {
+    nel *= (size_t)M;
+    nn *= (size_t)(M + 1);
+  }
+  const size_t nu = (size_t)N * nn;
+  std::vector<void *> tmp;
+  auto take = [&](auto **p, size_t count) {
+    cudaError_t e = dalloc(h, p, count);
+    if (e == cudaSuccess) tmp.push_back(*p);
+    return e;
+  };
+  auto release = [&]() {
+    for (void *q : tmp) dfree(h, q);
+    tmp.clear();
+  };
+  double *Eg = nullptr, *fg = nullptr, *work = nullptr, *Ud = nullptr, *rr = nullptr;
+  int *it_d = nullptr;
+  cudaError_t e = take(&Eg, nel * R * R);
+  if (e == cudaSuccess) e = take(&fg, nel * N);
+  if (e == cudaSuccess) e = take(&work, 4 * nu);
+  if (e == cudaSuccess) e = take(&rr, 1);
+  if (e == cudaSuccess) e = take(&it_d, 1);
+  const bool dev = is_device_ptr(U);
+  if (e == cudaSuccess && !dev) e = take(&Ud, nu);
+  if (e != cudaSuccess) {
+    release();
+    return cuda_fail(h, e, "macro buffers");
+  }
+  size_t covered = 0;
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    Level &L = h->lv[l];
+    const int np = L.npts;
+    if (!E[l] || !fbar[l]) {
+      release();
+      return set_err(h, MCH_ERR_ARG, "missing level coefficients");
+    }
+    std::vector<int> elem(np);
+    for (int p = 0; p < np; ++p) {
+      size_t flat = 0, stride = 1;
+      for (int a = 0; a < D; ++a) {
+        flat += (size_t)L.plan.points[(size_t)p * D + a] * stride;
+        stride *= (size_t)M;
+      }
+      elem[p] = (int)flat;
+    }
+    int *elem_d = nullptr;
+    double *El = nullptr, *fl = nullptr;
+    e = take(&elem_d, np);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(elem_d, elem.data(), np * sizeof(int), cudaMemcpyHostToDevice, h->st);
+    const double *Esrc = E[l], *fsrc = fbar[l];
+    if (e == cudaSuccess && !is_device_ptr(Esrc)) {
+      e = take(&El, (size_t)np * R * R);
+      if (e == cudaSuccess) e = stage(h, El, Esrc, (size_t)np * R * R * sizeof(double), true);
+      Esrc = El;
+    }
+    if (e == cudaSuccess && !is_device_ptr(fsrc)) {
+      e = take(&fl, (size_t)np * N);
+      if (e == cudaSuccess) e = stage(h, fl, fsrc, (size_t)np * N * sizeof(double), true);
+      fsrc = fl;
+    }
+    if (e == cudaSuccess) e = launch_macro_gather(np, R, N, elem_d, Esrc, fsrc, Eg, fg, h->st);
+    // the host vector must outlive its asynchronous copy
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) {
+      release();
+      return cuda_fail(h, e, "macro gather");
+    }
+    ++h->launches;
+    covered += (size_t)np;
+  }
+  if (covered != nel) {
+    release();
+    return set_err(h, MCH_ERR_ARG, "the levels do not cover the macro grid");
+  }
+  MacroSolveArgs a{};
+  a.dim = D;
+  a.M = M;
+  a.N = N;
+  a.R = R;
+  a.max_iter = max_iter;
+  a.H = spacing;
+  a.tol = tol;
+  a.E = Eg;
+  a.f = fg;
+  a.U = dev ? U : Ud;
+  a.r = work;
+  a.p = work + nu;
+  a.q = work + 2 * nu;
+  a.diag = work + 3 * nu;
+  a.iters = it_d;
+  a.relres = rr;
+  e = launch_macro_cg(a, h->st);
+  int it_h = 0;
+  double rr_h = 0.0;
+  if (e == cudaSuccess) {
+    ++h->launches;
+    if (!dev) {
+      e = cudaMemcpyAsync(U, Ud, nu * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+      h->d2h += (long long)(nu * sizeof(double));
+    }
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&it_h, it_d, sizeof(int), cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(&rr_h, rr, sizeof(double), cudaMemcpyDeviceToHost, h->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+  release();
+  if (e != cudaSuccess) return cuda_fail(h, e, "macro solve");
+  if (iters) *iters = it_h;
+  if (relres) *relres = rr_h;
+  if (!(rr_h <= tol)) {
+    if (it_h < max_iter) return set_err(h, MCH_ERR_BREAKDOWN, "macro system not positive definite");
+    return set_err(h, MCH_ERR_NOT_CONVERGED, "macro solve did not reach the tolerance");
+  }
+  return MCH_OK;
+}
+
 mch_status mch_set_timing(mch_handle *h, int enable) {
   if (!h) return MCH_ERR_ARG;
   if (enable && h->n_ev == 0) {

@@ -125,6 +125,37 @@ cudaError_t launch_gram(int npts, int R, int nv, const double *X, const double *
                         bool sym = false);
 
 // ---------------------------------------------------------------------------------------
+// Macroscopic problem (k_macro.cu)
+
+constexpr int MCH_MACRO_MAXN = 4;
+
+struct MacroSourceArgs {
+  int npts, dim, N, R, nf, lgr, nvf, P, overs;
+  const double *phi;       // [pts][R][nvf] cell functions on the level-1 lattice
+  const uint8_t *labels;   // [pts][(nf >> lgr)^d] level-n labels
+  const double *xp;        // [pts][dim] macropoint positions
+  double rve_len, alpha;
+  double w[MCH_MACRO_MAXN];  // source weight per continuum
+  double c[3];             // centre of the Gaussian
+  double *fbar;            // [pts][N]
+};
+cudaError_t launch_macro_source(const MacroSourceArgs &a, bool ffs, cudaStream_t st);
+// Eg[elem[p]] = E[p], fg[elem[p]] = fbar[p]
+cudaError_t launch_macro_gather(int npts, int R, int N, const int *elem, const double *E,
+                                const double *fbar, double *Eg, double *fg, cudaStream_t st);
+
+struct MacroSolveArgs {
+  int dim, M, N, R, max_iter;
+  double H, tol;
+  const double *E;   // [M^d][R][R] coefficient densities of the blocks (macro order)
+  const double *f;   // [M^d][N] source densities
+  double *U, *r, *p, *q, *diag;   // [N][(M+1)^d] solution and work vectors
+  int *iters;
+  double *relres;
+};
+cudaError_t launch_macro_cg(const MacroSolveArgs &a, cudaStream_t st);
+
+// ---------------------------------------------------------------------------------------
 // 3D (k3d.cuh conventions: (n+1)^3 lattice, nv = nv3_of(n))
 
 // Persistent cooperative level solve (k_level3d.cu). Vectors stream through global memory;
