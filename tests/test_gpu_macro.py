@@ -48,6 +48,7 @@ def _oracle_sources(wl, phis, med, w, c, alpha):
 
 
 CASES = [
+    ("channel2d_4x4_n32", dict(n_fine=32), "fp64"),   # one level; blocks tile the unit square
     ("channel2d_17x17_L3", dict(n_fine=64, macro_n=9, strides=(4, 2, 1)), "fp64"),
     ("channel2d_17x17_L3", dict(n_fine=64, macro_n=9, strides=(4, 2, 1)), "mixed"),
     ("incl2d_33x33_L4", dict(n_fine=128, macro_n=5, strides=(4, 2, 1)), "mixed"),
