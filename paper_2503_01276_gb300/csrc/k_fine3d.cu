@@ -116,14 +116,14 @@ __global__ void __launch_bounds__(F3_THREADS) k_interp3d(ChildArgs a) {
 }
 
 // y = h_f A_1 phi and g -= s C_1 phi: one thread per interior node column of the level-1
-// lattice, walking z with sliding windows; the constraint functionals go per element plane
-// into running sums in registers, per CTA into shared memory, then into g.
-template <class S>
+// lattice, walking z with sliding windows; the constraint functionals go per (element
+// column, label) into registers, per CTA into shared memory, then into g.
+template <int NCN, class S>
 __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double hf) {
   using V = typename S::V;
   const int unit = blockIdx.y, pt = unit / a.R, r = unit % a.R;
   const int nf = a.nf, W = nf + 1, ni = nf - 1, lgr = a.lgr, ncg = nf >> lgr;
-  const int P = 1 << a.lgP, nq = P * P * P;
+  const int P = 1 << a.lgP, mf = 1 << a.lgmf, nq = P * P * P;
   __shared__ double bins[MCH_MAX_NC3];
   for (int i = threadIdx.x; i < a.nc; i += F3_THREADS) bins[i] = 0.0;
   __syncthreads();
@@ -141,10 +141,8 @@ __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double
         return ff_load(a.kappa_ff, pt, ncg * ncg * ncg, (int)c);
       else return kc[c];
     };
-    const int nm1 = a.N - 1, pp2 = P * P;
     V v[3][3][3], kk[2][2][2];
-    // kappa of a plane of the four adjacent elements, and their labels packed one byte per
-    // element column c = 2 sy + sx (clamped so that no row index leaves the bins)
+    int lo[2][2], up[2][2];
     auto load_v = [&](V (&pl)[3][3], int z) {
 #pragma unroll
       for (int dy = 0; dy < 3; ++dy)
@@ -152,60 +150,57 @@ __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double
         for (int dx = 0; dx < 3; ++dx)
           pl[dy][dx] = S::ld(a.phi, unit, a.nvf, (int)(base + W2 * z + (dx - 1) + W * (dy - 1)));
     };
-    auto load_k = [&](V (&pl)[2][2], int ez) -> int {
-      int key = 0;
+    auto load_k = [&](V (&pl)[2][2], int (&lp)[2][2], int ez) {
 #pragma unroll
       for (int sy = 0; sy < 2; ++sy)
 #pragma unroll
         for (int sx = 0; sx < 2; ++sx) {
           const size_t c = cidx((kx - 1 + sx) >> lgr, (ky - 1 + sy) >> lgr, ez >> lgr, ncg);
           pl[sy][sx] = kval(c);
-          key |= min((int)lc[c], nm1) << (8 * (2 * sy + sx));
+          lp[sy][sx] = lc[c];
         }
-      return key;
     };
-    // sub-block index (within a z-block) of the element columns c = 2 sy + sx
-    int bxy[4];
-#pragma unroll
-    for (int c = 0; c < 4; ++c)
-      bxy[c] = ((ky - 1 + (c >> 1)) >> a.lgmf) * P + ((kx - 1 + (c & 1)) >> a.lgmf);
     load_v(v[0], 0);
     load_v(v[1], 1);
-    int klo = load_k(kk[0], 0);
-    // C_1 phi: one running sum per element plane (below and above the node), kept while the
-    // plane's four labels and its z-block stay the same and then added to the four element
-    // columns' rows
-    V alo = S::zero(), aup = S::zero();
-    int slo = -1, sup = -1, zlo = 0, zup = 0;  // the sums' label keys and z-block offsets
-    auto flush = [&](V &acc, int key, int zoff) {
-      if (key >= 0) {
-        const double d = S::to(acc);
-        if (d != 0.0) {
+    load_k(kk[0], lo, 0);
+    V acc[4][NCN];
 #pragma unroll
-          for (int c = 0; c < 4; ++c)
-            atomicAdd(&bins[((key >> (8 * c)) & 255) * nq + zoff + bxy[c]], d);
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+      for (int j = 0; j < NCN; ++j) acc[c][j] = S::zero();
+    int zb = 0;
+    auto flush = [&]() {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int ex = kx - 1 + (c & 1), ey = ky - 1 + (c >> 1);
+        const int bb = (zb * P + (ey >> a.lgmf)) * P + (ex >> a.lgmf);
+#pragma unroll
+        for (int j = 0; j < NCN; ++j) {
+          const double d = S::to(acc[c][j]);
+          if (d != 0.0) atomicAdd(&bins[j * nq + bb], d);
+          acc[c][j] = S::zero();
         }
       }
-      acc = S::zero();
     };
     for (int kz = 1; kz < nf; ++kz) {
       load_v(v[2], kz + 1);
-      const int kup = load_k(kk[1], kz);
+      load_k(kk[1], up, kz);
       const V val = v[1][1][1];
       S::st(a.y, unit, a.nvf, (int)(base + W2 * kz), hv * q1_apply3d_v<V>(v, kk, third, twelfth));
-      const int zl = ((kz - 1) >> a.lgmf) * pp2, zu = (kz >> a.lgmf) * pp2;
-      if (klo != slo || zl != zlo) {
-        flush(alo, slo, zlo);
-        slo = klo;
-        zlo = zl;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int j = 0; j < NCN; ++j)
+          if (lo[c >> 1][c & 1] == j) acc[c][j] += val;
+      if ((kz & (mf - 1)) == 0) {
+        flush();
+        zb = kz / mf;
       }
-      alo = alo + val;
-      if (kup != sup || zu != zup) {
-        flush(aup, sup, zup);
-        sup = kup;
-        zup = zu;
-      }
-      aup = aup + val;
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int j = 0; j < NCN; ++j)
+          if (up[c >> 1][c & 1] == j) acc[c][j] += val;
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -216,11 +211,12 @@ __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double
 #pragma unroll
       for (int i = 0; i < 2; ++i)
 #pragma unroll
-        for (int j = 0; j < 2; ++j) kk[0][i][j] = kk[1][i][j];
-      klo = kup;
+        for (int j = 0; j < 2; ++j) {
+          kk[0][i][j] = kk[1][i][j];
+          lo[i][j] = up[i][j];
+        }
     }
-    flush(alo, slo, zlo);
-    flush(aup, sup, zup);
+    flush();
   }
   __syncthreads();
   double *g = a.g + (size_t)pt * a.nc * a.R + r;
@@ -453,8 +449,13 @@ cudaError_t launch_fine_apply3d(const ChildArgs &a, double hf, cudaStream_t st, 
   if (a.nc > MCH_MAX_NC3 || (ffs && !a.kappa_ff)) return cudaErrorInvalidValue;
   const int ni = a.nf - 1;
   dim3 grid((ni * ni + F3_THREADS - 1) / F3_THREADS, a.npts * a.R);
-  if (ffs) k_fine_apply3d<FFS><<<grid, F3_THREADS, 0, st>>>(a, hf);
-  else k_fine_apply3d<F64S><<<grid, F3_THREADS, 0, st>>>(a, hf);
+  if (ffs) {
+    if (a.N <= 2) k_fine_apply3d<2, FFS><<<grid, F3_THREADS, 0, st>>>(a, hf);
+    else k_fine_apply3d<4, FFS><<<grid, F3_THREADS, 0, st>>>(a, hf);
+  } else {
+    if (a.N <= 2) k_fine_apply3d<2, F64S><<<grid, F3_THREADS, 0, st>>>(a, hf);
+    else k_fine_apply3d<4, F64S><<<grid, F3_THREADS, 0, st>>>(a, hf);
+  }
   return cudaGetLastError();
 }
 
