@@ -51,6 +51,7 @@ CASES = [
     ("channel2d_4x4_n32", dict(n_fine=32), "fp64"),   # one level; blocks tile the unit square
     ("channel2d_17x17_L3", dict(n_fine=64, macro_n=9, strides=(4, 2, 1)), "fp64"),
     ("channel2d_17x17_L3", dict(n_fine=64, macro_n=9, strides=(4, 2, 1)), "mixed"),
+    ("channel2d_17x17_L3", dict(n_fine=64, macro_n=9, strides=(4, 2, 1), overs=1), "mixed"),
     ("incl2d_33x33_L4", dict(n_fine=128, macro_n=5, strides=(4, 2, 1)), "mixed"),
     ("channel3d_9x9x9_L3", dict(n_fine=16, macro_n=3, strides=(2, 1), periods=2), "mixed"),
 ]
