@@ -40,6 +40,7 @@ class Workload:
     precision: str = "mixed"  # "fp64" | "mixed"
     interp: str = "multilinear"  # "multilinear" | "nearest1" (nearest point of S_1)
     overs: int = 0               # oversampling layers: R_p = central (P - 2 overs)^d periods
+    medium_periods: int = 0      # medium periods per RVE side (0: the constraint sub-blocks P)
 
     @property
     def n_rhs(self) -> int:

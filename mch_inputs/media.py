@@ -1,7 +1,8 @@
 """Synthetic high-contrast media on macropoint RVE grids.
 
 A medium is a global function of position built from periods of side
-eps = rve_len / P. Every RVE starts on a period boundary, so an element of
+eps = rve_len / P (P = the workload's medium_periods, by default its constraint
+sub-block count). Every RVE starts on a period boundary, so an element of
 an RVE grid with m = n / P elements per period sits at period-local
 coordinate t = (i mod m + 1/2) / m along each axis (exact in binary for the
 power-of-two m used here) inside global period K = K0 + i div m. All random
@@ -64,7 +65,7 @@ def macro_points_xyz(wl: Workload, idx: np.ndarray) -> np.ndarray:
 def _grids(wl: Workload, idx: np.ndarray, n: int):
     """Per point and element: global period index K and local coordinate t."""
     d = wl.dim
-    P = wl.periods
+    P = wl.medium_periods or wl.periods
     if n % P:
         raise ValueError(f"RVE grid {n} is not a multiple of the period count {P}")
     m = n // P

@@ -71,5 +71,9 @@ def test_descriptor_validation_without_gpu(mch):
     assert lib.mch_create(ctypes.byref(ov), None, ctypes.byref(h)) == 1
     ov = mch.desc_from_workload(mi.workload("channel3d_9x9x9_L3"), overs=1)
     assert lib.mch_create(ctypes.byref(ov), None, ctypes.byref(h)) == 8
+    # coarse blocks with one oversampling layer (3 sub-blocks per side): the kernels need a
+    # power-of-two sub-block count, so the configuration is refused, not mis-solved
+    ov = mch.desc_from_workload(wl, periods=3, overs=1)
+    assert lib.mch_create(ctypes.byref(ov), None, ctypes.byref(h)) == 8
     assert not h.value
     assert lib.mch_status_name(4) == b"MCH_ERR_ORDER"

@@ -145,6 +145,24 @@ def test_oversampling_matches_dense_kkt(d, n, P, overs):
     assert _rel(r["E"], r0["E"]) > 1e-6
 
 
+@pytest.mark.parametrize("d,n,mp", [(2, 48, 6)])
+def test_oversampled_coarse_blocks_match_dense_kkt(d, n, mp):
+    """The configuration of Sec. 2 and Sec. 5: R_p^+ = the coarse block K_p with l = 1 layer
+    of neighbouring blocks (3^d blocks, each a constraint sub-block R_q), R_p = K_p (o = 1),
+    and a medium whose period differs from the blocks (mp medium periods per RVE side);
+    against the dense brute force."""
+    name = "channel2d_17x17_L3" if d == 2 else "channel3d_9x9x9_L3"
+    wl = _small(name, n_fine=n, macro_n=3, strides=(1,))
+    wl = mi.small_workload(name, n_fine=n, macro_n=3, strides=(1,), periods=3, overs=1,
+                           medium_periods=mp, rve_len=3 * wl.spacing)
+    kap, lab = mi.media(wl, np.array([[1] * d]), n)
+    assert len(np.unique(lab[0])) == wl.n_cont
+    r = cell.solve_point(cell.LevelOps(wl, 1), kap[0], lab[0], overs=1)
+    Eb, Phib = bf.cell_E(d, n, wl.rve_len, kap[0], lab[0], wl.n_cont, 3, 1)
+    assert _rel(r["E"], Eb) < RTOL
+    assert _rel(r["Phi"], Phib.T) < 1e-10
+
+
 def test_child_correction_matches_dense_kkt():
     """Level-2 correction problem (Eqs. phi_avar_corrector, phi_grad_corrector)
     against the dense fine-grid KKT with the coarse basis evaluated pointwise."""
