@@ -77,3 +77,19 @@ def test_descriptor_validation_without_gpu(mch):
     assert lib.mch_create(ctypes.byref(ov), None, ctypes.byref(h)) == 8
     assert not h.value
     assert lib.mch_status_name(4) == b"MCH_ERR_ORDER"
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/mch.h is a C interface: it compiles as strict C99 with no warnings."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "mch.h"\nint main(void) { return mch_status_name(0) == 0; }\n')
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-fsyntax-only", "-I", inc, str(src)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
