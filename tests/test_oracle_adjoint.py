@@ -40,9 +40,17 @@ def test_euler_identity(strides, n_fine, macro, overs):
                                                         ((4, 2, 1), 64, 5, 0),
                                                         ((1,), 16, 3, 1), ((2, 1), 32, 3, 1)])
 def test_central_differences(strides, n_fine, macro, overs):
+    """Central differences with relative step 1e-6 on three elements of every level. The
+    oracle solves its saddle systems to ~1e-14 (FP64 refinement), so a loss value is accurate
+    to ~1e-14 sum |W||E| and a central difference to ~1e-14 sum |W||E| / h; the allowance is
+    100 times that (the Euler identity does not pin the hierarchical part of the gradient:
+    scaling every kappa leaves the cell functions unchanged, so the terms through the parents'
+    functions cancel in it; these differences do)."""
     wl, pl, med, W = _setup(strides, n_fine, macro, overs=overs)
     fwd = adjoint.forward(wl, pl, med)
     g = adjoint.backward(wl, pl, med, fwd, W)
+    swe = sum(float(np.sum(np.abs(W[n]) * np.abs(np.array([r["E"] for r in fwd[n]]))))
+              for n in range(len(pl)))
     rng = np.random.default_rng(11)
     checked = 0
     for n in range(len(pl)):
@@ -59,7 +67,7 @@ def test_central_differences(strides, n_fine, macro, overs):
                 out.append(_loss(wl, pl, [(k2[q], med[q][1]) for q in range(len(pl))], W))
             fd = (out[0] - out[1]) / (2 * h)
             scale = max(abs(g[n][i, e]), 1e-6 * np.abs(g[n]).max())
-            assert abs(fd - g[n][i, e]) <= 1e-5 * scale + 1e-9 * abs(out[0]) / h, (n, i, e, fd, g[n][i, e])
+            assert abs(fd - g[n][i, e]) <= 1e-5 * scale + 1e-12 * swe / h, (n, i, e, fd, g[n][i, e])
             checked += 1
     assert checked == 3 * len(pl)
 

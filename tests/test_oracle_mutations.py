@@ -4,9 +4,10 @@
 import numpy as np
 import pytest
 
+import test_oracle_adjoint as adj_pins
 import test_oracle_macro as pins
 import test_oracle_pins as cell_pins
-from oracle import cell, fe, macro
+from oracle import adjoint, cell, fe, macro, plan
 
 _assemble = macro.assemble
 _source = macro.source_point
@@ -118,4 +119,54 @@ def test_child_pin_catches_wrong_prolongation(monkeypatch):
     monkeypatch.setattr(cell, "prolong_medium", _prolong_swapped_axes)
     with pytest.raises(AssertionError):
         cell_pins.test_child_correction_matches_dense_kkt()
+
+
+# --------------------------------------------------------------------------- plan and adjoint
+
+_level_plan = plan.level_plan
+_point_adjoint = adjoint._point_adjoint
+
+
+def _plan_weights_on_wrong_vertices(wl):
+    # mistake: the multilinear weights attached to the vertices in reverse order
+    levels = _level_plan(wl)
+    for lev in levels:
+        lev["parents"] = [[(lv, pos, w) for (lv, pos, _), (_, _, w) in zip(par, par[::-1])]
+                          for par in lev["parents"]]
+    return levels
+
+
+def _adjoint_without_parent_seeds(wl, ops, kap, lab, r, W, V):
+    # mistake: the hierarchy is ignored in the reverse sweep (nothing pushed to the parents)
+    g, U = _point_adjoint(wl, ops, kap, lab, r, W, V)
+    return g, (None if U is None else np.zeros_like(U))
+
+
+def _adjoint_seed_sign(wl, ops, kap, lab, r, W, V):
+    # mistake: the terms added to the incoming seed V enter with the wrong sign
+    g, U = _point_adjoint(wl, ops, kap, lab, r, W, V)
+    return g, (None if U is None else 2 * V - U)
+
+
+def test_parent_pin_catches_weights_on_wrong_vertices(monkeypatch):
+    monkeypatch.setattr(plan, "level_plan", _plan_weights_on_wrong_vertices)
+    with pytest.raises(AssertionError):
+        cell_pins.test_level_plan_parents("channel2d_17x17_L3")
+
+
+@pytest.mark.parametrize("mutant", [_adjoint_without_parent_seeds, _adjoint_seed_sign])
+def test_difference_pin_catches_adjoint_mistakes(monkeypatch, mutant):
+    monkeypatch.setattr(adjoint, "_point_adjoint", mutant)
+    with pytest.raises(AssertionError):
+        adj_pins.test_central_differences((2, 1), 16, 3, 0)
+    with pytest.raises(AssertionError):
+        adj_pins.test_central_differences((2, 1), 32, 3, 1)
+
+
+@pytest.mark.parametrize("mutant", [_adjoint_without_parent_seeds, _adjoint_seed_sign])
+def test_euler_identity_is_blind_to_the_hierarchical_terms(monkeypatch, mutant):
+    """Documents why the differences are needed: the Euler identity still holds with these
+    mistakes (scaling every kappa leaves the cell functions unchanged)."""
+    monkeypatch.setattr(adjoint, "_point_adjoint", mutant)
+    adj_pins.test_euler_identity((2, 1), 16, 3, 0)
 
