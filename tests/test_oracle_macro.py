@@ -157,3 +157,18 @@ def test_macro_system_spd_with_hierarchy_coefficients():
     Ai = A[dof][:, dof].toarray()
     assert np.abs(Ai - Ai.T).max() < 1e-12 * np.abs(Ai).max()
     np.linalg.cholesky(0.5 * (Ai + Ai.T))
+
+
+def test_grid_from_levels_places_points_by_macro_index():
+    """Per-level arrays land at the flat macro index of their points (x fastest), and the
+    levels of the plan cover every macropoint exactly once."""
+    for name in ("channel2d_17x17_L3", "channel3d_9x9x9_L3"):
+        wl = mi.workload(name)
+        pl = plan.level_plan(wl)
+        M, d = wl.macro_n, wl.dim
+        vals = [np.asarray(lev["points"], dtype=np.float64) for lev in pl]   # value = index
+        g = macro.grid_from_levels(pl, M, d, vals)
+        want = np.stack(np.meshgrid(*[np.arange(M)] * d, indexing="ij")[::-1], -1).reshape(-1, d)
+        assert np.array_equal(g, want)
+        assert sum(len(lev["points"]) for lev in pl) == M ** d
+

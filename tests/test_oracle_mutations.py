@@ -170,3 +170,44 @@ def test_euler_identity_is_blind_to_the_hierarchical_terms(monkeypatch, mutant):
     monkeypatch.setattr(adjoint, "_point_adjoint", mutant)
     adj_pins.test_euler_identity((2, 1), 16, 3, 0)
 
+
+# --------------------------------------------------------------------------- more cell pieces
+
+_saddle = cell.saddle_solve
+_region = fe.Grid.region_mask
+_grid_from_levels = macro.grid_from_levels
+
+
+def _correction_rhs_sign(A, C, b, g, *args, **kw):
+    # mistake: the correction right-hand side taken as +P^T A_1 I
+    return _saddle(A, C, -b, g, *args, **kw)
+
+
+def _region_ignores_overs(self, periods, overs):
+    # mistake: E integrated over the whole RVE whatever the oversampling
+    return _region(self, periods, 0)
+
+
+def _grid_y_fastest(pl, M, d, per_level):
+    # mistake: macro order with y fastest
+    g = _grid_from_levels(pl, M, d, per_level)
+    return g.reshape((M,) * d + g.shape[1:]).swapaxes(0, 1).reshape(g.shape)
+
+
+def test_child_pin_catches_correction_sign(monkeypatch):
+    monkeypatch.setattr(cell, "saddle_solve", _correction_rhs_sign)
+    with pytest.raises(AssertionError):
+        cell_pins.test_child_correction_matches_dense_kkt()
+
+
+def test_oversampling_pin_catches_ignored_region(monkeypatch):
+    monkeypatch.setattr(fe.Grid, "region_mask", _region_ignores_overs)
+    with pytest.raises(AssertionError):
+        cell_pins.test_oversampling_matches_dense_kkt(2, 16, 4, 1)
+
+
+def test_macro_order_pin_catches_transposed_grid(monkeypatch):
+    monkeypatch.setattr(macro, "grid_from_levels", _grid_y_fastest)
+    with pytest.raises(AssertionError):
+        pins.test_grid_from_levels_places_points_by_macro_index()
+
