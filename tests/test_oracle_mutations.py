@@ -211,3 +211,21 @@ def test_macro_order_pin_catches_transposed_grid(monkeypatch):
     with pytest.raises(AssertionError):
         pins.test_grid_from_levels_places_points_by_macro_index()
 
+
+_prolongation = fe.prolongation
+
+
+def _prolongation_swapped_coarse_axes(gc, gf):
+    # mistake: the coarse nodal values read with x and y exchanged
+    P = _prolongation(gc, gf).tocsc()
+    W = gc.n + 1
+    k = np.arange(gc.n_nodes)
+    swapped = (k % W) * W + (k // W) % W + (k // (W * W)) * W * W
+    return P[:, swapped].tocsr()
+
+
+def test_galerkin_pin_catches_wrong_prolongation(monkeypatch):
+    monkeypatch.setattr(fe, "prolongation", _prolongation_swapped_coarse_axes)
+    with pytest.raises(AssertionError):
+        cell_pins.test_galerkin_identities()
+
