@@ -260,9 +260,17 @@ mch_status mch_macro_solve(mch_handle *h, const double *const *E, const double *
  *   E [n_points][R][R] FP64, R = n_cont * 3: device memory, overwritten.
  *   precision MCH_MIXED or MCH_FP64; rtol as in mch_desc (0 -> 1e-8). 2D only.
  * Work is enqueued on cuda_stream (a cudaStream_t, NULL = legacy default stream), which is
- * synchronised once before returning. The first call on a device looks up the buffer's
- * device address while that device is current, so make it before any stream capture. Calls
- * share the buffer: calls that overlap on the GPU (other streams, other host threads) race.
+ * synchronised once before returning; a stream that is being captured is refused with
+ * MCH_ERR_ARG, so never call this inside a stream capture.
+ * Set-up: with CUDA's lazy module loading (the default) the driver creates the buffer, and
+ * loads each kernel's code, at first use on a device, so the first call on a device, and the
+ * first call with another n_elem, n_cont or precision, may allocate. Make one call with the
+ * sizes and precision that later calls use, while that device is current and before its
+ * memory is handed to a caching allocator; every later call with them allocates nothing.
+ * The buffer's device address is looked up on every call (no address is cached), so calls
+ * after a cudaDeviceReset are safe.
+ * Calls share the buffer: calls that overlap on the GPU (other streams, other host threads)
+ * race on it.
  * The paper has no counterpart to this entry point. */
 mch_status mch_direct_noalloc(int n_cont, int n_elem, int periods, double rve_len, int precision,
                               double rtol, int n_points, const double *kappa,

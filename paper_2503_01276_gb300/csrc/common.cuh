@@ -20,6 +20,18 @@
 namespace mch {
 
 __host__ __device__ __forceinline__ int round_up(int a, int b) { return (a + b - 1) / b * b; }
+
+// Streaming multiprocessors of the current device (grid sizing); 1 if the query fails.
+inline int device_sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      sms < 1) {
+    cudaGetLastError();
+    return 1;
+  }
+  return sms;
+}
 __host__ __device__ __forceinline__ int nv_of(int n) { return round_up((n + 1) * (n + 1), 32); }
 
 template <typename T>

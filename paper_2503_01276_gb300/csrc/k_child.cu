@@ -306,7 +306,7 @@ cudaError_t gram_s(int npts, int R, int nv, const double *X, const double *Y, do
   int slices = nv >= 8192 ? 8 : (nv >= 2048 ? 4 : 1);
   if (nv > 100000) {
     // 3D level-1 lattices: enough slices for every SM when the level has few points
-    const int want = (4 * 152 + npts - 1) / npts;
+    const int want = (4 * device_sm_count() + npts - 1) / npts;
     slices = want < 8 ? 8 : (want > nv / 4096 ? nv / 4096 : want);
   }
   dim3 grid(npts, slices);

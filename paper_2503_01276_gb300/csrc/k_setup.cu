@@ -276,7 +276,7 @@ cudaError_t launch_setup2d(const SetupArgs &a, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMemsetAsync(a.status, 0, sizeof(int) * a.npts, st);
   if (e != cudaSuccess) return e;
   // enough slices to give every SM a few CTAs when the level has few points
-  int slices = (4 * 152 + a.npts - 1) / a.npts;
+  int slices = (4 * device_sm_count() + a.npts - 1) / a.npts;
   slices = slices < 1 ? 1 : (slices > (a.n + 1) / 4 ? (a.n + 1) / 4 : slices);
   k_setup_nodes<<<dim3(a.npts, slices), SN_THREADS, 0, st>>>(a, slices);
   e = cudaGetLastError();

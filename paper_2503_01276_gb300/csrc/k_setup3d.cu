@@ -244,7 +244,7 @@ cudaError_t launch_setup3d(const SetupArgs &a, cudaStream_t st) {
   if (e == cudaSuccess) e = cudaMemsetAsync(a.bacc, 0, sizeof(double) * a.npts * a.nc * 4, st);
   if (e == cudaSuccess) e = cudaMemsetAsync(a.status, 0, sizeof(int) * a.npts, st);
   if (e != cudaSuccess) return e;
-  int slices = (4 * 152 + a.npts - 1) / a.npts;
+  int slices = (4 * device_sm_count() + a.npts - 1) / a.npts;
   slices = slices < 1 ? 1 : (slices > (a.n + 1) / 2 ? (a.n + 1) / 2 : slices);
   const size_t smem_n = sizeof(double) * ((size_t)a.nc * a.nc + 4 * a.nc);
   e = cudaFuncSetAttribute(k_setup3d_nodes, cudaFuncAttributeMaxDynamicSharedMemorySize,

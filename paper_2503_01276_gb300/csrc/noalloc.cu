@@ -11,9 +11,16 @@
 //
 // The buffer is a file-scope __device__ array of MCH_NOALLOC_SCRATCH_BYTES, so every GPU
 // that loads the library holds it until the process exits. In host code the array's name
-// is only a host-side stand-in for the symbol, never a device address; the device address is
-// looked up once per device with cudaGetSymbolAddress, on the first call made while that
-// device is current (that first call should therefore come before any stream capture).
+// is only a host-side stand-in for the symbol, never a device address: every call looks up
+// the device address with cudaGetSymbolAddress while the caller's device is current (a
+// table lookup once the module is loaded), so no address is cached across calls, threads or
+// a cudaDeviceReset. With CUDA's lazy module loading (the default) the driver creates the
+// array when this file's module is first used on a device, and loads each kernel's code at its
+// first launch: so the first call on a device, and the first call with another grid size or
+// precision (other kernel instantiations), may allocate. A caller makes one call with the
+// sizes and precision it will use at start-up, before its device memory is handed to a
+// caching allocator; later calls with them allocate nothing. Calls on a capturing stream are
+// refused (every call synchronises its stream to read the convergence record).
 // All calls share the buffer and it keeps the last call's contents: the parts that must
 // start at zero are cleared on every call, and calls that overlap on the GPU (on different
 // streams, or from different host threads) race on it.
@@ -27,9 +34,6 @@ namespace mch {
 namespace {
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[MCH_NOALLOC_SCRATCH_BYTES];
-
-constexpr int kMaxDevices = 64;
-unsigned char *g_scratch_ptr[kMaxDevices] = {};
 
 int ilog2i(int v) {
   int r = 0;
@@ -65,10 +69,23 @@ extern "C" mch_status mch_direct_noalloc(int n_cont, int n_elem, int periods, do
                                          int precision, double rtol, int n_points,
                                          const double *kappa, const uint8_t *labels, double *E,
                                          void *cuda_stream) {
+  // the buffer's device address on the current device (loads the module on first use)
+  void *sym = nullptr;
+  if (cudaGetSymbolAddress(&sym, g_noalloc_scratch) != cudaSuccess || !sym) {
+    cudaGetLastError();
+    return MCH_ERR_CUDA;
+  }
   const int d = 2, N = n_cont, n = n_elem, P = periods;
   if (N < 1 || N > MCH_MAX_CONT || n_points < 1 || !(rve_len > 0) || !kappa || !labels || !E ||
       (precision != MCH_FP64 && precision != MCH_MIXED) || rtol < 0)
     return MCH_ERR_ARG;
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return MCH_ERR_CUDA;
+  }
+  if (cap != cudaStreamCaptureStatusNone) return MCH_ERR_ARG;
   const bool fp64 = precision == MCH_FP64;
   if (!level2d_supported(n, P, fp64)) return MCH_ERR_UNSUPPORTED;
   const int R = N * (1 + d), nc = N * P * P;
@@ -100,18 +117,7 @@ extern "C" mch_status mch_direct_noalloc(int n_cont, int n_elem, int periods, do
   const size_t o_sum = take(4 * sizeof(double));
   if (off > (size_t)MCH_NOALLOC_SCRATCH_BYTES) return MCH_ERR_OOM;
 
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MCH_ERR_CUDA;
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
-      return MCH_ERR_CUDA;
-    }
-    g_scratch_ptr[dev] = static_cast<unsigned char *>(p);
-  }
-  unsigned char *base = g_scratch_ptr[dev];
-  cudaStream_t st = (cudaStream_t)cuda_stream;
+  unsigned char *base = static_cast<unsigned char *>(sym);
   auto D = [&](size_t o) { return reinterpret_cast<double *>(base + o); };
   auto I = [&](size_t o) { return reinterpret_cast<int *>(base + o); };
 
