@@ -122,6 +122,9 @@ typedef struct {
   double final_ms;          /* effective coefficients and cell-function assembly    */
   int pcg_launches;         /* PCG sweep launches                                   */
   long long pcg_node_iters; /* sum over units of PCG iterations x interior nodes    */
+  long long pcg_node_applies; /* sum over units of inner stencil applications x interior
+                               nodes (PCG iterations times the preconditioner's Chebyshev
+                               steps, plus its first application per sweep)            */
 } mch_level_stats;
 
 /* Validates the descriptor, builds the level plan (Eq. defi_Sn; parents and multilinear

@@ -42,7 +42,7 @@ class MchLevelStats(C.Structure):
                 ("h2d_bytes", C.c_longlong), ("d2h_bytes", C.c_longlong),
                 ("setup_ms", C.c_double), ("interp_ms", C.c_double), ("pcg_ms", C.c_double),
                 ("prep_ms", C.c_double), ("final_ms", C.c_double), ("pcg_launches", C.c_int),
-                ("pcg_node_iters", C.c_longlong)]
+                ("pcg_node_iters", C.c_longlong), ("pcg_node_applies", C.c_longlong)]
 
 
 def load_library(path: str = LIB_PATH) -> C.CDLL:

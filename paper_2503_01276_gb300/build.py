@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmch.so")
-SOURCES = ["api.cu", "plan.cpp", "k_setup.cu", "k_level_f32.cu", "k_level_f32_alt.cu", "k_level_f64.cu", "k_fp64.cu", "k_child.cu", "k_adjoint.cu", "noalloc.cu", "k_setup3d.cu", "k_level3d.cu", "k_fine3d.cu", "k_macro.cu"]
+SOURCES = ["api.cu", "plan.cpp", "k_setup.cu", "k_level_f32.cu", "k_level_f32_alt.cu", "k_level_f32_alt2.cu", "k_level_f64.cu", "k_fp64.cu", "k_child.cu", "k_adjoint.cu", "noalloc.cu", "k_setup3d.cu", "k_level3d.cu", "k_fine3d.cu", "k_macro.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(HERE, "..", "include")]

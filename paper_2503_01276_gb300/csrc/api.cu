@@ -187,7 +187,7 @@ double rho_pow(const mch_handle *h, int rho) {
 cudaError_t launch_child(mch_handle *h, Level &L, double *g, int *nl = nullptr) {
   const mch_desc &d = h->d;
   ChildArgs ca{L.npts, h->R, d.n_fine, ilog2(L.rho), L.nvf, h->slots, ilog2(d.n_fine / d.periods),
-               ilog2(d.periods), d.n_cont, h->nc, L.par_ptr, L.par_w, L.kappa, L.labels, L.phi,
+               d.periods, d.n_cont, h->nc, L.par_ptr, L.par_w, L.kappa, L.labels, L.phi,
                h->yfine, g, 1.0 / rho_pow(h, L.rho), h->yfineR, d.overs, L.kapff};
   if (d.dim == 2) {
     if (nl) *nl = 1;
@@ -767,8 +767,12 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
   }
   for (size_t u = 0; u < np * R; ++u) S.sweeps = std::max(S.sweeps, sweeps[u]);
   S.pcg_launches = solve_launches;
-  for (size_t u = 0; u < np * R; ++u)
-    S.pcg_node_iters += (long long)iters[u] * (long long)(L.n - 1) * (L.n - 1) * (d3 ? L.n - 1 : 1);
+  const long long nodes = (long long)(L.n - 1) * (L.n - 1) * (d3 ? L.n - 1 : 1);
+  const int nch = d3 ? 1 : level2d_cheb_steps(L.n, fp64, L.variant);
+  for (size_t u = 0; u < np * R; ++u) {
+    S.pcg_node_iters += (long long)iters[u] * nodes;
+    S.pcg_node_applies += ((long long)iters[u] * nch + (long long)sweeps[u] * (nch - 1)) * nodes;
+  }
   for (size_t k = 1; k < tags.size(); ++k) {
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, h->ev[k - 1], h->ev[k]), "event time");
@@ -1235,7 +1239,7 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
     const size_t np = L.npts;
     CK(stage(h, h->Wd, dL_dE[li], np * R * R * sizeof(double), true), "stage dL/dE");
     const bool seeds = L.V != nullptr;
-    AdjArgs aa{(int)np, R, d.n_fine, ilog2(L.rho), nvf, L.nv, nc, ilog2(d.n_fine / P), ilog2(P),
+    AdjArgs aa{(int)np, R, d.n_fine, ilog2(L.rho), nvf, L.nv, nc, ilog2(d.n_fine / P), P,
                h->slots, inv_vol, 1.0 / rho_pow(h, L.rho), h->Wd, L.phi,
                seeds ? h->yc : nullptr, L.lam, seeds ? h->lamadj : nullptr, L.kappa, L.labels,
                L.V, h->psi1, h->psi2, h->dk, L.par_V, L.par_w, h->ffs ? 1 : 0, d.overs};

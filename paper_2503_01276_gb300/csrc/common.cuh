@@ -54,85 +54,6 @@ __device__ __forceinline__ void add_by_label(T (&acc)[MCH_MAX_CONT], int lab, T 
   for (int j = 0; j < MCH_MAX_CONT; ++j) acc[j] += (lab == j) ? v : T(0);
 }
 
-// Column-strip mapping used by every node kernel: lane c of a row of `n` threads owns node
-// column kx = c + 1 (active for c < n - 1) and row group G owns node rows
-// [1 + G*rpt, 1 + (G+1)*rpt). With rpt dividing m = n / P, the elements adjacent to a
-// thread's nodes lie in the thread's "main" sub-block (column c / m, row G*rpt / m) except
-// the east elements of lanes with (c+1) % m == 0 and the north elements of the strip's last
-// row when (G+1)*rpt is a multiple of m. Main-block contributions are accumulated per label
-// in registers; the others go straight to shared-memory bins.
-struct Strip {
-  int n, lgm, lgP, lgnq;
-  int c, kx;       // lane column, node column
-  int G, rpt;      // global row group, rows per thread
-  int bxm, bym;    // main sub-block
-  bool east_out;   // east elements belong to the next sub-block column
-  __device__ __forceinline__ void init(int n_, int lgm_, int lgP_, int lane_col, int row_group,
-                                       int rpt_) {
-    n = n_;
-    lgm = lgm_;
-    lgP = lgP_;
-    lgnq = 2 * lgP_;
-    c = lane_col;
-    kx = lane_col + 1;
-    G = row_group;
-    rpt = rpt_;
-    bxm = c >> lgm;
-    bym = (G * rpt) >> lgm;
-    east_out = ((c + 1) & ((1 << lgm) - 1)) == 0;
-  }
-  __device__ __forceinline__ int bin(int lab, int ex, int ey) const {
-    return (lab << lgnq) + ((ey >> lgm) << lgP) + (ex >> lgm);
-  }
-};
-
-// Adds v (a node value) to the four constraint rows of the node's adjacent elements with
-// labels lSW, lSE, lNW, lNE; node row ky. Main-sub-block contributions go to acc[label],
-// the rest is added atomically to bins[].
-template <typename T>
-__device__ __forceinline__ void scatter_node(const Strip &s, int ky, int lSW, int lSE, int lNW,
-                                             int lNE, T v, T (&acc)[MCH_MAX_CONT], T *bins) {
-  const bool north_out = (ky >> s.lgm) != s.bym;  // element row ky outside the main block row
-  // south elements (row ky-1) are always in the main block row
-  add_by_label(acc, lSW, v);
-  if (!s.east_out) add_by_label(acc, lSE, v);
-  else atomicAdd(&bins[s.bin(lSE, s.c + 1, ky - 1)], v);
-  if (!north_out) {
-    add_by_label(acc, lNW, v);
-    if (!s.east_out) add_by_label(acc, lNE, v);
-    else atomicAdd(&bins[s.bin(lNE, s.c + 1, ky)], v);
-  } else {
-    atomicAdd(&bins[s.bin(lNW, s.c, ky)], v);
-    atomicAdd(&bins[s.bin(lNE, s.c + 1, ky)], v);
-  }
-}
-
-// Reduces the per-label register accumulators over the lanes that share the main sub-block
-// (aligned groups of min(m, 32) lanes within a warp; callers guarantee the alignment) and
-// adds the group sums to bins[]. All 32 lanes of the warp must call it.
-template <typename T>
-__device__ __forceinline__ void flush_acc(const Strip &s, T (&acc)[MCH_MAX_CONT], int n_cont,
-                                          T *bins, bool lane_has_strip) {
-  const int m = 1 << s.lgm;
-  const int seg = m < 32 ? m : 32;
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int j = 0; j < MCH_MAX_CONT; ++j) {
-    if (j >= n_cont) break;
-    T v = seg_sum(acc[j], seg);
-    if ((lane & (seg - 1)) == 0 && lane_has_strip && v != T(0))
-      atomicAdd(&bins[(j << s.lgnq) + (s.bym << s.lgP) + s.bxm], v);
-  }
-}
-
-// Ct^T lambda at a node: sum of lambda over the rows of its four adjacent elements.
-template <typename T>
-__device__ __forceinline__ T ct_lambda(const Strip &s, int ky, int lSW, int lSE, int lNW, int lNE,
-                                       const T *lam) {
-  return lam[s.bin(lSW, s.c, ky - 1)] + lam[s.bin(lSE, s.c + 1, ky - 1)] +
-         lam[s.bin(lNW, s.c, ky)] + lam[s.bin(lNE, s.c + 1, ky)];
-}
-
 // 2D Q1 stencil at a node from the four adjacent kappas (a = SW, b = SE, c = NW, d = NE;
 // h^{d-2} = 1 in 2D) and the 3x3 neighbourhood of x. Element matrix entries 2/3 (same node),
 // -1/6 (edge neighbour), -1/3 (opposite corner).

@@ -78,7 +78,7 @@ __global__ void k_adj_grad2d(AdjArgs a) {
   if (a.overs) {
     // direct term sum_rs W_rs Phi_r^T Khat Phi_s / |R_p| on elements inside R_p (R_p is a
     // union of level-n elements: test one fine element's period)
-    const int P = 1 << a.lgP, o = a.overs;
+    const int P = a.P, o = a.overs;
     const int px = (Ex * rho) >> a.lgmf, py = (Ey * rho) >> a.lgmf;
     if (px >= o && px < P - o && py >= o && py < P - o) {
       const double *Wp = a.W + (size_t)pt * R * R;
@@ -133,7 +133,7 @@ __global__ void k_adj_seed2d(AdjArgs a) {
   const int unit = blockIdx.y;
   const int R = a.R, pt = unit / R, r = unit % R;
   const int nf = a.nf, Wf = nf + 1, lgr = a.lgr, ncg = nf >> lgr, nc = a.nc;
-  const int lgmf = a.lgmf, lgP = a.lgP;
+  const int lgmf = a.lgmf, P = a.P, nq = a.P * a.P;
   __shared__ double sig[MCH_MAX_NC];
   // sigma = sum_s What_rs lambda_s - lambda'_r, scaled by rho^-2
   for (int b = threadIdx.x; b < nc; b += blockDim.x) {
@@ -154,10 +154,10 @@ __global__ void k_adj_seed2d(AdjArgs a) {
   const uint8_t *lc = a.labels_c + (size_t)pt * ncg * ncg;
   const double *ps = a.psi1 + ((size_t)pt * R + r) * a.nvf + k;
   auto K = [&](int ex, int ey) { return kc[(ex >> lgr) + ncg * (ey >> lgr)]; };
-  const int Nm1 = (nc >> (2 * lgP)) - 1;
+  const int Nm1 = nc / nq - 1;
   auto bin = [&](int ex, int ey) {
     const int l = min((int)lc[(ex >> lgr) + ncg * (ey >> lgr)], Nm1);
-    return (l << (2 * lgP)) + ((ey >> lgmf) << lgP) + (ex >> lgmf);
+    return l * nq + (ey >> lgmf) * P + (ex >> lgmf);
   };
   double u = q1_apply(K(fx - 1, fy - 1), K(fx, fy - 1), K(fx - 1, fy), K(fx, fy), ps[-Wf - 1],
                       ps[-Wf], ps[-Wf + 1], ps[-1], ps[0], ps[1], ps[Wf - 1], ps[Wf], ps[Wf + 1]);
@@ -179,7 +179,7 @@ __global__ void k_adj_own2d(AdjArgs a) {
   if (k >= Wf * Wf) return;
   const int fx = k % Wf, fy = k / Wf;
   if (fx == 0 || fy == 0 || fx == nf || fy == nf) return;
-  const int P = 1 << a.lgP, o = a.overs;
+  const int P = a.P, o = a.overs;
   const double *kc = a.kappa_c + (size_t)pt * ncg * ncg;
   auto K = [&](int ex, int ey) {
     const int px = ex >> a.lgmf, py = ey >> a.lgmf;

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
       if (a.yR) {
         // the same with kappa zero outside the integration region (period index of each
         // adjacent fine element)
-        const int P = 1 << a.lgP, o = a.overs;
+        const int P = a.P, o = a.overs;
         auto in = [&](int ex, int ey) {
           const int px = ex >> a.lgmf, py = ey >> a.lgmf;
           return px >= o && px < P - o && py >= o && py < P - o;
@@ -114,13 +114,15 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
   }
 
   // C_1 I on the band's element rows: element corner sums per (label, sub-block). Warp w
-  // takes column chunk w % nch (32 element columns, one sub-block column or aligned
-  // halves of one) and every (8 / nch)-th row.
+  // takes column chunk w % nch (32 element columns: whole sub-block columns or aligned
+  // parts of one; lanes past the last column add nothing) and every rstep-th row, rstep =
+  // 8 / nch; warps beyond nch * rstep have no rows.
   {
     const int warp = tid >> 5, lane = tid & 31;
-    const int nch = nf >> 5;                       // nf >= 32
+    const int nch = (nf + 31) >> 5;                // nf <= 256
     const int chunk = warp % nch, rstep = (CF_THREADS / 32) / nch;
     const int ex = chunk * 32 + lane;
+    const bool lane_ok = ex < nf;
     const int lgm = a.lgmf, m = 1 << lgm;
     const int seg = m < 32 ? m : 32;
     const uint8_t *lc = a.labels_c + (size_t)pt * ncg * ncg;
@@ -134,24 +136,27 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
       for (int j = 0; j < NC; ++j) {
         const double sj = S::to(seg_sum_s<S>(acc[j], seg));
         if ((lane & (seg - 1)) == 0 && sj != 0.0)
-          atomicAdd(&bins[(j << (2 * a.lgP)) + (by << a.lgP) + bx], sj);
+          atomicAdd(&bins[j * a.P * a.P + by * a.P + bx], sj);
         acc[j] = S::zero();
       }
     };
     // rows of one warp share ey, so the flush condition is uniform over the warp
     int by_cur = -1;
-    for (int ey = row_lo + warp / nch; ey < erow_hi; ey += rstep) {
+    const int ey0 = warp < nch * rstep ? row_lo + warp / nch : erow_hi;
+    for (int ey = ey0; ey < erow_hi; ey += rstep) {
       const int by = ey >> lgm;
       if (by != by_cur) {
         if (by_cur >= 0) flush(by_cur);
         by_cur = by;
       }
-      const V *tr = tile + (ey - row_lo + 1) * W + ex;
-      const V sv = (tr[0] + tr[1]) + (tr[W] + tr[W + 1]);
-      const int l = lc[(ex >> lgr) + ncg * (ey >> lgr)];
+      if (lane_ok) {
+        const V *tr = tile + (ey - row_lo + 1) * W + ex;
+        const V sv = (tr[0] + tr[1]) + (tr[W] + tr[W + 1]);
+        const int l = lc[(ex >> lgr) + ncg * (ey >> lgr)];
 #pragma unroll
-      for (int j = 0; j < NC; ++j)
-        if (l == j) acc[j] += sv;
+        for (int j = 0; j < NC; ++j)
+          if (l == j) acc[j] += sv;
+      }
     }
     if (by_cur >= 0) flush(by_cur);
   }

@@ -123,7 +123,7 @@ __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double
   using V = typename S::V;
   const int unit = blockIdx.y, pt = unit / a.R, r = unit % a.R;
   const int nf = a.nf, W = nf + 1, ni = nf - 1, lgr = a.lgr, ncg = nf >> lgr;
-  const int P = 1 << a.lgP, mf = 1 << a.lgmf, nq = P * P * P;
+  const int P = a.P, mf = 1 << a.lgmf, nq = P * P * P;
   __shared__ double bins[MCH_MAX_NC3];
   for (int i = threadIdx.x; i < a.nc; i += F3_THREADS) bins[i] = 0.0;
   __syncthreads();
@@ -381,7 +381,7 @@ __global__ void __launch_bounds__(F3_THREADS) k_adj_seed3d(AdjArgs a, double hf)
   const int unit = blockIdx.y;
   const int R = a.R, pt = unit / R, r = unit % R;
   const int nf = a.nf, Wf = nf + 1, lgr = a.lgr, ncg = nf >> lgr, nc = a.nc;
-  const int lgmf = a.lgmf, lgP = a.lgP, P = 1 << lgP;
+  const int lgmf = a.lgmf, P = a.P, nq3 = P * P * P;
   __shared__ double sig[MCH_MAX_NC3];
   for (int b = threadIdx.x; b < nc; b += F3_THREADS) {
     double sgm = 0.0;
@@ -417,8 +417,8 @@ __global__ void __launch_bounds__(F3_THREADS) k_adj_seed3d(AdjArgs a, double hf)
         const int ex = fx - 1 + sx, ey = fy - 1 + sy, ez = fz - 1 + sz;
         const size_t c = cidx(ex >> lgr, ey >> lgr, ez >> lgr, ncg);
         kk[sz][sy][sx] = kc[c];
-        const int l = min((int)lc[c], (nc >> (3 * lgP)) - 1);
-        const int bin = (l << (3 * lgP)) + (((ez >> lgmf) * P + (ey >> lgmf)) << lgP) + (ex >> lgmf);
+        const int l = min((int)lc[c], nc / nq3 - 1);
+        const int bin = l * nq3 + ((ez >> lgmf) * P + (ey >> lgmf)) * P + (ex >> lgmf);
         u += sig[bin];
       }
   u += hf * q1_apply3d<double>(v, kk);

@@ -60,6 +60,9 @@ bool level2d_supported(int n, int P, bool fp64);
 int level2d_variant_count(int n, bool fp64);
 bool level2d_variant_ok(int n, int P, bool fp64, int v);
 cudaError_t launch_level2d_alt(const LevelArgs<float> &a, cudaStream_t st);
+// Chebyshev steps of the preconditioner of launch shape v (1 = Jacobi): every PCG iteration
+// applies the stencil this many times (k_level.cuh).
+int level2d_cheb_steps(int n, bool fp64, int v);
 
 // y = A(kappa) x + cb * b on an n-grid whose kappa lives on the (n/rho)-grid (piecewise
 // constant), for a batch of vectors; FP64.
@@ -103,7 +106,7 @@ cudaError_t launch_from_ff(int count, const double *src, int nvs, double *dst, i
 // Fine-grid work of a child level (k_child.cu): I = sum_t w_t Phi_t into phi, y = A_1 I, and
 // g -= s * C_1 I (g holds the targets on entry).
 struct ChildArgs {
-  int npts, R, nf, lgr, nvf, slots, lgmf, lgP, N, nc;
+  int npts, R, nf, lgr, nvf, slots, lgmf, P, N, nc;   // P sub-blocks per side, mf = 2^lgmf
   const double *const *par_ptr;   // [pt][slots] parent cell functions (R vectors each)
   const double *par_w;            // [pt][slots]
   const double *kappa_c;          // [pt][(nf >> lgr)^2]
@@ -207,7 +210,7 @@ cudaError_t launch_prolong_add3d(int npts, int R, int nf, int rho, const double 
 
 // Backward pass kernels (k_adjoint.cu).
 struct AdjArgs {
-  int npts, R, nf, lgr, nvf, nvc, nc, lgmf, lgP, slots;
+  int npts, R, nf, lgr, nvf, nvc, nc, lgmf, P, slots;  // P sub-blocks per side
   double inv_vol, inv_rho2;
   const double *W;          // [pt][R][R] dL/dE
   const double *phi;        // [pt][R][nvf] cell functions (level-1 grid)

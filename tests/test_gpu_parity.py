@@ -234,3 +234,41 @@ def test_invalid_medium_reported():
     with pytest.raises(mch.MchError) as e:
         s.solve_level(1, kap, lab)
     assert e.value.name == "MCH_ERR_DEGENERATE"
+
+
+def _coarse_block_workload(n_fine, macro, strides, precision, mp=6):
+    """Sec. 2 and Sec. 5: R_p^+ = the coarse block K_p with l = 1 layer of neighbouring
+    blocks, so the constraint sub-blocks R_q are 3 x 3 coarse blocks (P = 3, odd), R_p = K_p
+    (o = 1), and the medium's period (mp per RVE side) differs from the blocks."""
+    wl = mi.small_workload("channel2d_17x17_L3", n_fine=n_fine, macro_n=macro, strides=strides)
+    return mi.small_workload("channel2d_17x17_L3", n_fine=n_fine, macro_n=macro,
+                             strides=strides, periods=3, overs=1, medium_periods=mp,
+                             rve_len=3 * wl.spacing, precision=precision)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_coarse_blocks_odd_P_single_level(precision):
+    """The configuration pinned against the dense brute force in the oracle pins (48 x 48
+    RVE, 3 x 3 coarse blocks, o = 1, six medium periods per side), every point of a 3 x 3
+    macrogrid: E and the cell functions against the oracle."""
+    wl = _coarse_block_workload(48, 3, (1,), precision)
+    s, Eg = _run_gpu(wl, rtol=1e-11)
+    Eo = _run_oracle(wl)
+    err = block_rel_err(Eg[0], Eo[0]["E"], wl.n_cont, wl.dim)
+    assert err < 1e-9, err
+    phi = s.cell_functions(1)
+    ref = Eo[0]["Phi"]
+    scale = np.abs(ref).max(axis=2, keepdims=True) + 1e-300
+    assert (np.abs(phi - ref) / scale).max() < 1e-9
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_coarse_blocks_odd_P_hierarchy(precision):
+    """Three levels (RVE grids 96 / 48 / 24) with 3 x 3 coarse blocks and o = 1 on a 5 x 5
+    macrogrid: every level against the oracle."""
+    wl = _coarse_block_workload(96, 5, (4, 2, 1), precision)
+    s, Eg = _run_gpu(wl, rtol=1e-11)
+    Eo = _run_oracle(wl)
+    for lev in range(wl.n_levels):
+        err = block_rel_err(Eg[lev], Eo[lev]["E"], wl.n_cont, wl.dim)
+        assert err < 1e-9, (lev + 1, err)
