@@ -65,6 +65,10 @@ import mch_inputs as mi  # noqa: E402
 
 METRIC = "cell-problem RHS solved/s at 1e-6 rel. accuracy; stencil HBM GB/s vs peak"
 WORKLOAD = "incl2d_33x33_L4"   # the benchmark workload (--workload selects others)
+# refinement tolerance of every solve: the projected-residual ratio at which the effective
+# coefficients of every level are within 1e-6 (block-relative) of the oracle on every workload
+# of the suite, checked by the oracle legs
+RTOL = 3e-9
 # the other workloads of the suite, each reported as a record of "configs"
 SUB_RECORDS = (("channel2d_4x4_n32", "fp64"), ("channel2d_17x17_L3", "fp64"),
                ("channel2d_17x17_L3", "mixed"), ("channel3d_9x9x9_L3", "mixed"),
@@ -259,11 +263,15 @@ def cpu_leg_main(spec_file):
                 need = parallel.closure(wl, targets)
             jd = pool.job(wl, need, _media_fn(wl))
             E, wall, tsum, walls = pool.run(jd, wl, need)
-            err = max(block_rel_err(Eg[lv - 1][i], E[(lv, i)], wl.n_cont, wl.dim)
-                      for (lv, i) in targets)
+            errs = {}
+            for (lv, i) in targets:
+                e = block_rel_err(Eg[lv - 1][i], E[(lv, i)], wl.n_cont, wl.dim)
+                errs[lv] = max(errs.get(lv, 0.0), e)
+            err = max(errs.values())
             n_solved = sum(len(v) for v in need.values())
             results[rec["tag"]] = {
-                "err": err, "points_checked": len(targets), "points_solved": n_solved,
+                "err": err, "err_by_level": [errs.get(lv) for lv in range(1, wl.n_levels + 1)],
+                "points_checked": len(targets), "points_solved": n_solved,
                 "wall_s": wall, "single_core_s": tsum, "level_wall_s": walls,
                 "rhs_solved": n_solved * wl.n_rhs, "cores": pool.procs}
     print(json.dumps({"cpu": results}), flush=True)
@@ -344,11 +352,11 @@ def run_reference(args, rank, world):
 class GpuRun:
     """One workload on the GPU: handle, resident and pinned media, timed steps."""
 
-    def __init__(self, wl, dev, stream, tiles=None, autotune=True, **solver_kw):
+    def __init__(self, wl, dev, stream, tiles=None, autotune=True, rtol=RTOL, **solver_kw):
         import torch
         import paper_2503_01276_gb300 as mch
         self.wl, self.dev, self.stream = wl, dev, stream
-        self.s = mch.Solver.from_workload(wl, stream=stream.cuda_stream, **solver_kw)
+        self.s = mch.Solver.from_workload(wl, stream=stream.cuda_stream, rtol=rtol, **solver_kw)
         self.s.set_timing(True)
         self.L = wl.n_levels
         self.med_host, self.med_dev = [], []
@@ -495,13 +503,19 @@ def roofline(wl, R, t, steps, tiles):
                         "peak_derived_source": "SMs x 128 FP32 lanes x 2 x sampled SM clock"}}
     bpn = BYTES3D_PER_NODE_ITER_UNIT + BYTES3D_PER_NODE_ITER_POINT / R
     node_iters = sum(l["node_iters"] for l in t["levels"])
+    by_level = []
+    for k, l in enumerate(t["levels"]):
+        by_level.append({"n": wl.n_level(k + 1), "ms_per_step": l["pcg_ms"] / steps,
+                         "gbs": (l["node_iters"] * bpn / (l["pcg_ms"] / 1e3) / 1e9)
+                         if l["pcg_ms"] > 0 else None})
     gbs = node_iters * bpn / (pcg_ms / 1e3) / 1e9 if pcg_ms > 0 else None
     return {"bound": "hbm", "kernel": "k_level3d (cooperative level solve)",
             "achieved": gbs, "peak": hbm, "unit": "GB/s",
             "frac": (gbs / hbm) if gbs else None, "traffic": None, "peak_source": hbm_src,
             "bytes_model": "per inner PCG iteration and interior node: 40 B of FP32 vectors "
                            "per function + 14 B of per-point data shared by the R functions",
-            "bytes_per_node_iteration": bpn, "kernel_share_of_step": share,
+            "bytes_per_node_iteration": bpn, "by_level": by_level,
+            "kernel_share_of_step": share,
             "launches_timed": sum(l["launches"] for l in t["levels"])}
 
 
@@ -531,13 +545,13 @@ def macro_leg(s, wl, E_dev, stream):
             "max_abs_u": float(U.abs().max().item())}
 
 
-def plain_fp64_leg(wl, med_dev, flush, steps, stream):
+def plain_fp64_leg(wl, med_dev, flush, steps, stream, rtol=RTOL):
     """The unbatched FP64 comparator: same workload and media, FP64 PCG, one macropoint per
     constrained-solve launch. Returns RHS/s, ms per step and the largest residual ratio."""
     import torch
     import paper_2503_01276_gb300 as mch
     s = mch.Solver.from_workload(wl, stream=stream.cuda_stream, precision="fp64",
-                                 point_batch=1)
+                                 point_batch=1, rtol=rtol)
     L = wl.n_levels
     E = [torch.zeros((s.num_points(l), s.R, s.R), dtype=torch.float64, device=flush.device)
          for l in range(1, L + 1)]
@@ -572,7 +586,7 @@ def plain_fp64_leg(wl, med_dev, flush, steps, stream):
     return out, E
 
 
-def backward_leg(wl, dev, stream, flush, reps=2):
+def backward_leg(wl, dev, stream, flush, reps=2, rtol=RTOL):
     """Forward then backward of the loss L = sum_p sum W[p] . E[p] (seeded N(0,1) weights on
     the upper triangles of the exchange and permeability blocks, seed 7), with the cell
     functions of the parents checkpointed (keep_parents = 1) or recomputed (0). Times the
@@ -589,7 +603,8 @@ def backward_leg(wl, dev, stream, flush, reps=2):
     out = {}
     grads = {}
     for kp in (1, 0):
-        s = mch.Solver.from_workload(wl, stream=stream.cuda_stream, keep_parents=kp)
+        s = mch.Solver.from_workload(wl, stream=stream.cuda_stream, keep_parents=kp,
+                                     rtol=rtol)
         L = wl.n_levels
         med = []
         for lev in range(1, L + 1):
@@ -628,9 +643,9 @@ def backward_leg(wl, dev, stream, flush, reps=2):
     return out
 
 
-def gpu_record(wl, dev, stream, flush, steps, warmup, e2e_steps):
+def gpu_record(wl, dev, stream, flush, steps, warmup, e2e_steps, rtol=RTOL):
     """A per-workload record (N = 1): RHS/s, e2e, roofline, launches, residual."""
-    g = GpuRun(wl, dev, stream)
+    g = GpuRun(wl, dev, stream, rtol=rtol)
     t = g.timed(steps, warmup, flush)
     total = float(np.sum(t["step_ms"])) / 1e3
     value = g.rhs_per_step * steps / total
@@ -664,6 +679,9 @@ def main():
                     help="skip the records of the other workloads")
     ap.add_argument("--workload", default=WORKLOAD,
                     help="workload of mch_inputs (default: the benchmark workload)")
+    ap.add_argument("--rtol", type=float, default=RTOL,
+                    help="refinement tolerance of the solves (the accuracy the metric names "
+                         "is checked against the oracle)")
     ap.add_argument("--tiles", default=None,
                     help="comma-separated launch shapes per level instead of autotuning "
                          "(fixed launch counts, for profiling)")
@@ -693,7 +711,7 @@ def main():
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     tiles = [int(v) for v in args.tiles.split(",")] if args.tiles else None
 
-    g = GpuRun(wl, dev, stream, tiles=tiles)
+    g = GpuRun(wl, dev, stream, tiles=tiles, rtol=args.rtol)
     t = g.timed(args.steps, args.warmup, flush, dist if world > 1 else None, world)
     t_total = max_over_ranks(float(np.sum(t["step_ms"])) / 1e3, dist if world > 1 else None, dev)
     value = whole_job_rate(g.rhs_per_step, world, args.steps, t_total)
@@ -726,7 +744,7 @@ def main():
             sub_steps = max(3, min(args.steps, 5 if swl.dim == 3 else 10))
             try:
                 rec, E, med_dev = gpu_record(swl, dev, stream, flush, sub_steps, 3,
-                                             max(3, sub_steps // 2))
+                                             max(3, sub_steps // 2), rtol=args.rtol)
             except Exception as ex:
                 configs.append({"workload": name, "precision": prec,
                                 "error": f"{type(ex).__name__}: {ex}"[:300]})
@@ -745,11 +763,11 @@ def main():
                            "reduced grids in the tests"}
             if name == ADJOINT_WORKLOAD:
                 try:
-                    rec["backward"] = backward_leg(swl, dev, stream, flush)
+                    rec["backward"] = backward_leg(swl, dev, stream, flush, rtol=args.rtol)
                 except Exception as ex:
                     rec["backward"] = {"error": f"{type(ex).__name__}: {ex}"[:300]}
             if name == PLAIN_WORKLOAD and prec == "mixed" and not args.no_plain:
-                plain, E_plain = plain_fp64_leg(swl, med_dev, flush, 2, stream)
+                plain, E_plain = plain_fp64_leg(swl, med_dev, flush, 2, stream, args.rtol)
                 plain["workload"] = name
                 plain["speedup_of_mixed_batched"] = rec["value"] / plain["value"]
                 sys.path.insert(0, os.path.join(ROOT, "tests"))
@@ -762,7 +780,7 @@ def main():
             torch.cuda.empty_cache()
 
     cpu = None
-    acc_err = None
+    acc_err = acc_levels = None
     if not args.no_cpu:
         res = run_cpu_leg(cpu_records)
         if "error" in res:
@@ -770,6 +788,7 @@ def main():
         else:
             m = res.get("main", {})
             acc_err = m.get("err")
+            acc_levels = m.get("err_by_level")
             if m:
                 cpu = {"value": m["rhs_solved"] / m["wall_s"], "unit": "RHS/s",
                        "cores": m["cores"], "kind": "oracle",
@@ -783,6 +802,7 @@ def main():
                 r = res.get(rec.get("tag"))
                 if r:
                     rec["accuracy"] = {"block_rel_err_vs_oracle": r["err"],
+                                       "block_rel_err_by_level": r["err_by_level"],
                                        "points_checked": r["points_checked"]}
                     rec["cpu_baseline"] = {"value": r["rhs_solved"] / r["wall_s"],
                                            "unit": "RHS/s", "cores": r["cores"],
@@ -801,7 +821,9 @@ def main():
             "e2e": {"value": e2e_value, "unit": "RHS/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": d2h},
             "gpu_launches": t["launches"], "clocks": t["clocks"],
-            "accuracy": {"max_relres": t["relres"], "block_rel_err_vs_oracle": acc_err,
+            "accuracy": {"max_relres": t["relres"], "rtol": args.rtol,
+                         "block_rel_err_vs_oracle": acc_err,
+                         "block_rel_err_by_level": acc_levels,
                          "points_checked": "all" if acc_err is not None else 0},
             "configs": configs, "plain_fp64_per_point": plain, "macro": macro_info}
     print(json.dumps(line), flush=True)

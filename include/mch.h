@@ -164,6 +164,28 @@ mch_status mch_level_parents(const mch_handle *h, int level, int32_t *parent_lev
  * residuals are reported by mch_level_stats. */
 mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const uint8_t *labels);
 
+/* One level of a hierarchy shared by several handles (one per GPU): the macropoints of a
+ * level are independent (Algorithm 1, lines 4-6), so each handle solves a contiguous range
+ * [p0, p1) of them and the children of every level read their parents' cell functions,
+ * which the other handles computed (Eq. phiXiI_all). This call solves points p0..p1-1 of
+ * `level` exactly as mch_solve_level would; kappa and labels hold those p1 - p0 points only
+ * ([p1 - p0][n^d], host or device). Every parent of the range must have cell functions on
+ * this handle: solved here, or imported with mch_set_cell_functions. An empty range
+ * (p0 == p1) only marks the level as complete on this handle (after its cell functions
+ * were imported). Coefficients, iteration counts and cell functions of points outside the
+ * ranges solved here are not computed (mch_effective_coeffs and mch_cell_functions still
+ * copy whole levels). mch_backward refuses a handle that solved any level by ranges
+ * (MCH_ERR_ORDER). MCH_ERR_ARG for a range outside [0, n_points]. */
+mch_status mch_solve_level_range(mch_handle *h, int level, int p0, int p1, const double *kappa,
+                                 const uint8_t *labels);
+
+/* Imports the cell functions of points p0..p1-1 of `level`, computed by another handle (the
+ * exchange step of a hierarchy split over several GPUs): phi [p1 - p0][R][(n_fine+1)^d] FP64
+ * on the level-1 lattice (the layout of mch_cell_functions), host or device; copied (and in
+ * mixed precision stored as float-float) into the library's storage, where the children of
+ * later levels read them. Synchronises the handle's stream. */
+mch_status mch_set_cell_functions(mch_handle *h, int level, int p0, int p1, const double *phi);
+
 /* Copies the level's effective coefficients E [n_points][R][R] FP64 to `E` (host or device).
  * Optional outputs (NULL to skip): iters [n_points][R] int32 total PCG iterations, relres
  * [n_points][R] FP64 final projected residual ratio. */

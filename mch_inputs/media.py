@@ -20,6 +20,12 @@ Families (continuum labels in parentheses):
                   disc of radius 0.15 eps at (eps/2, 0.7 eps) (label 1,
                   kappa = 1e3 exp(0.5 Z), Z ~ N(0,1) per period); matrix
                   (label 2, kappa = 1).
+  layered2d       periodic layers: channel rows [1/4, 1/2) of every period (label 0,
+                  kappa = contrast), matrix elsewhere (label 1, kappa = 1); both
+                  times the slowly varying g = 2 + sin(pi x) sin(pi y) of Sec. 4.
+                  No random draw, and the layer edges fall on element edges of every
+                  grid with at least 4 elements per period, so every level of a
+                  hierarchy sees the same layers (only g is sampled per grid).
   channel3d       channel along x with square cross-section [3/8, 5/8)^2 in
                   (y, z) period coordinates (label 0, kappa = contrast);
                   matrix (label 1, kappa = 1); both times
@@ -100,6 +106,11 @@ def media(wl: Workload, idx, n: int):
         chan = (t[1] >= lo) & (t[1] < hi)
         labels = np.where(chan, 0, 1).astype(np.uint8)
         g = 1.0 + 0.5 * np.sin(2 * np.pi * x[0]) * np.sin(2 * np.pi * x[1])
+        kappa = np.where(chan, wl.contrast, 1.0) * g
+    elif wl.family == "layered2d":
+        chan = (t[1] >= 1.0 / 4.0) & (t[1] < 1.0 / 2.0)
+        labels = np.where(chan, 0, 1).astype(np.uint8)
+        g = 2.0 + np.sin(np.pi * x[0]) * np.sin(np.pi * x[1])
         kappa = np.where(chan, wl.contrast, 1.0) * g
     elif wl.family == "channel_incl2d":
         u = counter_uniform(seed, 1, K[0], K[1])

@@ -64,6 +64,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "mch_level_points": (C.c_int, [P, C.c_int, P]),
         "mch_level_parents": (C.c_int, [P, C.c_int, P, P, P]),
         "mch_solve_level": (C.c_int, [P, C.c_int, P, P]),
+        "mch_solve_level_range": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P, P]),
+        "mch_set_cell_functions": (C.c_int, [P, C.c_int, C.c_int, C.c_int, P]),
         "mch_effective_coeffs": (C.c_int, [P, C.c_int, P, P, P]),
         "mch_cell_functions": (C.c_int, [P, C.c_int, P]),
         "mch_level_stats_get": (C.c_int, [P, C.c_int, C.POINTER(MchLevelStats)]),
@@ -213,6 +215,23 @@ class Solver:
             return st
         self._check(st, "mch_solve_level")
         return st
+
+    def solve_level_range(self, level: int, p0: int, p1: int, kappa=None, labels=None,
+                          allow_not_converged: bool = False) -> int:
+        """Points [p0, p1) of a level (mch_solve_level_range); kappa and labels hold those
+        points only."""
+        st = _LIB.mch_solve_level_range(self._h, level, int(p0), int(p1), _ptr(kappa),
+                                        _ptr(labels))
+        if st == 5 and allow_not_converged:
+            return st
+        self._check(st, "mch_solve_level_range")
+        return st
+
+    def set_cell_functions(self, level: int, p0: int, p1: int, phi):
+        """Imports the cell functions [p1 - p0][R][(n_fine + 1)^d] of points [p0, p1) of a
+        level (mch_set_cell_functions)."""
+        self._check(_LIB.mch_set_cell_functions(self._h, level, int(p0), int(p1), _ptr(phi)),
+                    "mch_set_cell_functions")
 
     def prepare_level(self, level: int, kappa, labels):
         """Stages inputs and computes the constraint data of a level on the side stream

@@ -46,6 +46,7 @@ struct Level {
   double *V = nullptr;            // [pt][R][nvf] backward seeds (levels with children)
   double **par_V = nullptr;       // [pt][slots] parents' seed blocks (levels > 1)
   bool solved = false;
+  bool partial = false;           // solved by mch_solve_level_range for a part of its points
   // mch_prepare_level: staged inputs and constraint data computed on the side stream
   bool prepared = false;
   const double *prep_kappa = nullptr;
@@ -336,6 +337,43 @@ cudaError_t restore_phi(mch_handle *h) {
   return cudaStreamSynchronize(h->st);
 }
 
+// The points [p0, p1) of a level as a level of their own: every per-point array offset by p0
+// (the plan's parent tables included), npts = p1 - p0. Flags stay with the real level.
+Level range_view(const Level &L, int p0, int p1, int dim, int R, int nc, int slots) {
+  Level V = L;
+  const size_t o = (size_t)p0, ne = elems(dim, L.n);
+  auto off = [&](auto *p, size_t per) { return p ? p + o * per : p; };
+  V.npts = p1 - p0;
+  V.kappa = off(L.kappa, ne);
+  V.labels = off(L.labels, ne);
+  V.G = off(L.G, (size_t)nc * R);
+  V.gI = off(L.gI, (size_t)nc * R);
+  V.Sinv64 = off(L.Sinv64, (size_t)nc * nc);
+  V.Sacc = off(L.Sacc, (size_t)nc * nc);
+  V.bacc = off(L.bacc, (size_t)nc * (dim + 1));
+  V.Sinv32 = off(L.Sinv32, (size_t)nc * nc);
+  V.kap32 = off(L.kap32, ne);
+  V.minv32 = off(L.minv32, (size_t)L.nv);
+  V.kapff = off(L.kapff, ne);
+  V.x = off(L.x, (size_t)R * L.nv);
+  V.b = off(L.b, (size_t)R * L.nv);
+  V.minv = off(L.minv, (size_t)L.nv);
+  V.ratio = off(L.ratio, (size_t)R);
+  V.iters = off(L.iters, (size_t)R);
+  V.sweeps = off(L.sweeps, (size_t)R);
+  V.ustat = off(L.ustat, (size_t)R);
+  V.pstat = off(L.pstat, 1);
+  V.dropped = off(L.dropped, 1);
+  V.E = off(L.E, (size_t)R * R);
+  V.phi = off(L.phi, (size_t)R * L.nvf);
+  V.par_ptr = off(L.par_ptr, (size_t)slots);
+  V.par_w = off(L.par_w, (size_t)slots);
+  V.lam = off(L.lam, (size_t)R * nc);
+  V.V = off(L.V, (size_t)R * L.nvf);
+  V.par_V = off(L.par_V, (size_t)slots);
+  return V;
+}
+
 // Stages the level's kappa and labels and computes its constraint data on stream `on`;
 // returns the number of kernels launched through *nl.
 cudaError_t setup_level(mch_handle *h, Level &L, const double *kappa, const uint8_t *labels,
@@ -579,15 +617,23 @@ mch_status mch_level_parents(const mch_handle *h, int level, int32_t *parent_lev
   return MCH_OK;
 }
 
-mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const uint8_t *labels) {
-  if (!valid_level(h, level) || !kappa || !labels) return set_err(h, MCH_ERR_ARG, "bad argument");
+}  // extern "C"
+
+namespace {
+
+// Algorithm 1, lines 4-6, for the points [p0, p1) of a level (all of them from
+// mch_solve_level); kappa and labels hold those points only.
+mch_status solve_range(mch_handle *h, int level, int p0, int p1, const double *kappa,
+                       const uint8_t *labels) {
   const int li = level - 1;
   for (int k = 0; k < li; ++k)
     if (!h->lv[k].solved)
       return set_err(h, MCH_ERR_ORDER, "level " + std::to_string(level) +
                                            " needs level " + std::to_string(k + 1) + " first");
   CK(restore_phi(h), "recompute cell functions");
-  Level &L = h->lv[li];
+  Level &L0 = h->lv[li];
+  const bool whole = p0 == 0 && p1 == L0.npts;
+  Level L = range_view(L0, p0, p1, h->d.dim, h->R, h->nc, h->slots);
   const mch_desc &d = h->d;
   const int R = h->R, nc = h->nc, N = d.n_cont, P = d.periods;
   const size_t np = L.npts, ne = elems(d.dim, L.n);
@@ -596,7 +642,8 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
   cudaStream_t st = h->st;
   h->h2d = h->d2h = 0;
   h->launches = 0;
-  L.solved = false;
+  L0.solved = false;
+  L0.partial = !whole;
 
   // phase marks for optional event timing: tag 0 setup, 1 interp, 2 pcg, 3 prep, 4 final
   std::vector<int> tags;
@@ -610,16 +657,16 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
   // with the same buffers)
   CK(mark(-1), "event");
   // a pending preparation writes this level's buffers on the side stream: always wait for it
-  if (L.prepared) CK(cudaStreamWaitEvent(st, L.prep_ev, 0), "wait for prepared level");
-  if (L.prepared && L.prep_kappa == kappa && L.prep_labels == labels) {
-    h->launches += L.prep_launches;
-    h->h2d += L.prep_h2d;
+  if (L0.prepared) CK(cudaStreamWaitEvent(st, L0.prep_ev, 0), "wait for prepared level");
+  if (whole && L0.prepared && L0.prep_kappa == kappa && L0.prep_labels == labels) {
+    h->launches += L0.prep_launches;
+    h->h2d += L0.prep_h2d;
   } else {
     int nl = 0;
     CK(setup_level(h, L, kappa, labels, st, &nl), "setup");
     h->launches += nl;
   }
-  L.prepared = false;
+  L0.prepared = false;
   CK(mark(0), "event");
 
   // |R_p| = the central (P - 2 overs)^d periods (the whole RVE when overs = 0)
@@ -686,7 +733,7 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
                           L.Sinv64 + p0 * nc * nc, L.minv + p0 * L.nv, g + p0 * nc * R, bb,
                           L.x + u0 * L.nv, L.iters + u0, L.sweeps + u0, L.ratio + u0,
                           L.ustat + u0, (float)d.inner_tol, max_iter, d.rtol, d.max_refine, lam,
-                          bvec ? h->bnorm + u0 : nullptr, L.variant};
+                          bvec ? h->bnorm + u0 : nullptr, L0.variant};
       CK(launch_level2d<float>(la, st), "level fp32");
     }
     ++h->launches;
@@ -740,7 +787,7 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
      "read ratio");
   CK(cudaStreamSynchronize(st), "level sync");
 
-  mch_level_stats &S = L.stats;
+  mch_level_stats &S = L0.stats;
   S = mch_level_stats{};
   S.n_points = (int)np;
   S.n_elem = L.n;
@@ -768,7 +815,7 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
   for (size_t u = 0; u < np * R; ++u) S.sweeps = std::max(S.sweeps, sweeps[u]);
   S.pcg_launches = solve_launches;
   const long long nodes = (long long)(L.n - 1) * (L.n - 1) * (d3 ? L.n - 1 : 1);
-  const int nch = d3 ? 1 : level2d_cheb_steps(L.n, fp64, L.variant);
+  const int nch = d3 ? 1 : level2d_cheb_steps(L.n, fp64, L0.variant);
   for (size_t u = 0; u < np * R; ++u) {
     S.pcg_node_iters += (long long)iters[u] * nodes;
     S.pcg_node_applies += ((long long)iters[u] * nch + (long long)sweeps[u] * (nch - 1)) * nodes;
@@ -792,7 +839,7 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
                    "point " + std::to_string(bad_pt) + " has flags " +
                        std::to_string(pstat[bad_pt]) +
                        " (1 kappa<=0, 2 label>=n_cont, 4 singular constraints, 8 absent continuum)");
-  L.solved = true;
+  L0.solved = true;
   if (!d.keep_parents && li == d.n_levels - 1) CK(release_phi(h), "release cell functions");
   if (breakdown)
     return set_err(h, MCH_ERR_BREAKDOWN, "PCG breakdown at unit " + std::to_string(bad_unit));
@@ -802,6 +849,65 @@ mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const 
     return set_err(h, MCH_ERR_NOT_CONVERGED, buf);
   }
   h->err.clear();
+  return MCH_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+mch_status mch_solve_level(mch_handle *h, int level, const double *kappa, const uint8_t *labels) {
+  if (!valid_level(h, level) || !kappa || !labels) return set_err(h, MCH_ERR_ARG, "bad argument");
+  return solve_range(h, level, 0, h->lv[level - 1].npts, kappa, labels);
+}
+
+mch_status mch_solve_level_range(mch_handle *h, int level, int p0, int p1, const double *kappa,
+                                 const uint8_t *labels) {
+  if (!valid_level(h, level)) return set_err(h, MCH_ERR_ARG, "bad argument");
+  Level &L = h->lv[level - 1];
+  if (p0 < 0 || p1 < p0 || p1 > L.npts) return set_err(h, MCH_ERR_ARG, "bad point range");
+  if (p0 == p1) {
+    // no point of this level here: the level is complete once its cell functions have been
+    // imported (mch_set_cell_functions)
+    for (int k = 0; k < level - 1; ++k)
+      if (!h->lv[k].solved) return set_err(h, MCH_ERR_ORDER, "earlier level not solved");
+    L.solved = true;
+    L.partial = true;
+    return MCH_OK;
+  }
+  if (!kappa || !labels) return set_err(h, MCH_ERR_ARG, "bad argument");
+  return solve_range(h, level, p0, p1, kappa, labels);
+}
+
+mch_status mch_set_cell_functions(mch_handle *h, int level, int p0, int p1, const double *phi) {
+  if (!valid_level(h, level) || !phi) return set_err(h, MCH_ERR_ARG, "bad argument");
+  Level &L = h->lv[level - 1];
+  if (p0 < 0 || p1 < p0 || p1 > L.npts) return set_err(h, MCH_ERR_ARG, "bad point range");
+  if (p0 == p1) return MCH_OK;
+  CK(restore_phi(h), "recompute cell functions");
+  const size_t W = (size_t)h->d.n_fine + 1;
+  const size_t len = h->d.dim == 3 ? W * W * W : W * W;
+  const size_t rows = (size_t)(p1 - p0) * h->R;
+  double *dst = L.phi + (size_t)p0 * h->R * L.nvf;
+  const bool dev = is_device_ptr(phi);
+  if (!dev) h->h2d += (long long)(rows * len * sizeof(double));
+  if (h->ffs) {
+    // FP64 -> float-float planes, through the level-1-grid scratch for host sources
+    const double *src = phi;
+    if (!dev) {
+      CK(cudaMemcpyAsync(h->yfine, phi, rows * len * sizeof(double), cudaMemcpyHostToDevice,
+                         h->st),
+         "stage cell functions");
+      src = h->yfine;
+    }
+    CK(launch_to_ff((int)rows, src, (int)len, dst, L.nvf, (int)len, h->st), "convert phi");
+  } else {
+    CK(cudaMemcpy2DAsync(dst, (size_t)L.nvf * sizeof(double), phi, len * sizeof(double),
+                         len * sizeof(double), rows,
+                         dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, h->st),
+       "copy phi");
+  }
+  CK(cudaStreamSynchronize(h->st), "sync");
   return MCH_OK;
 }
 
@@ -1172,6 +1278,8 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
   const int Lv = d.n_levels, R = h->R, nc = h->nc, N = d.n_cont, P = d.periods;
   for (int l = 0; l < Lv; ++l) {
     if (!h->lv[l].solved) return set_err(h, MCH_ERR_ORDER, "every level must be solved first");
+    if (h->lv[l].partial)
+      return set_err(h, MCH_ERR_ORDER, "the backward pass needs every point solved on this handle");
     if (!dL_dE[l] || !dL_dkappa[l]) return set_err(h, MCH_ERR_ARG, "null gradient buffer");
   }
   cudaStream_t st = h->st;

@@ -1,10 +1,17 @@
-"""Hierarchical (HMH) against direct (MH) effective coefficients on the 17x17 channel
-workload: every macropoint solved directly on the 128x128 RVE grid versus the three-level
-hierarchy (grids 128/64/32) with multilinear interpolation and with the single nearest S_1
-parent. The block-relative difference per level is the error of the hierarchical
-approximation on these media (the analogue of the paper's Type-3 comparison, which it
-reports for the macroscopic solutions of its own media); it is printed, and level 1 (solved
-identically by both) must agree to the solver tolerance."""
+"""Hierarchical (HMH) against direct (MH) effective coefficients, per workload: every
+macropoint solved directly on the level-1 RVE grid versus the hierarchy. The block-relative
+difference per level is the error of the hierarchical approximation on these media (the
+analogue of the paper's Type-3 comparison, Sec. 4, which it reports for the macroscopic
+solutions of its own media); it is printed per level, and level 1 (solved identically by
+both) must agree to the solver tolerance.
+
+The periodic control is the 17x17 three-level workload on a layered medium (the same layers
+in every period, edges on element edges of every level grid, times the slowly varying
+g = 2 + sin(pi x) sin(pi y) of Sec. 4): the paper reports hierarchical and direct results
+that agree closely for layered media, and so must this one. The channel media of the other
+workloads draw the channel offset per period and place the channel where a 4-element-per-
+period grid cannot follow it, so their coarse levels see a different medium and differ much
+more."""
 import numpy as np
 import pytest
 
@@ -31,22 +38,40 @@ def _solve(wl):
         for p, e in zip(pts, E):
             out[tuple(int(v) for v in p)] = (lev, e)
     s.close()
+    torch.cuda.empty_cache()
     return out
 
 
-def test_hmh_vs_direct_report():
-    base = mi.workload("channel2d_17x17_L3")
-    direct = _solve(mi.workload("channel2d_17x17_L3", strides=(1,), n_levels=1))
-    lines = []
-    for interp in ("multilinear", "nearest1"):
-        hmh = _solve(mi.workload("channel2d_17x17_L3", interp=interp))
+def _report(base, interps=("multilinear",)):
+    direct = _solve(mi.workload(base.name, family=base.family, strides=(1,), n_levels=1))
+    lines, worst = [], {}
+    for interp in interps:
+        hmh = _solve(mi.workload(base.name, family=base.family, interp=interp))
         for lev in range(1, base.n_levels + 1):
             errs = [block_rel_err(e, direct[p][1], base.n_cont, base.dim)
                     for p, (lv, e) in hmh.items() if lv == lev]
-            lines.append(f"{interp:11s} level {lev} ({len(errs)} points, grid "
-                         f"{base.n_level(lev)}): block-rel diff vs direct max {max(errs):.3e} "
-                         f"median {float(np.median(errs)):.3e}")
-            if lev == 1:
-                assert max(errs) < 1e-6
+            lines.append(f"{base.name} {base.family} {interp:11s} level {lev} ({len(errs)} "
+                         f"points, grid {base.n_level(lev)}): block-rel diff vs direct max "
+                         f"{max(errs):.3e} median {float(np.median(errs)):.3e}")
+            worst[(interp, lev)] = (max(errs), float(np.median(errs)))
             assert np.isfinite(max(errs))
     print("\n" + "\n".join(lines))
+    for interp in interps:
+        assert worst[(interp, 1)][0] < 1e-6
+    return worst
+
+
+def test_hmh_vs_direct_periodic_control():
+    base = mi.workload("channel2d_17x17_L3", family="layered2d")
+    worst = _report(base)
+    for lev in (2, 3):
+        assert worst[("multilinear", lev)][0] < 5e-3, (lev, worst)
+
+
+@pytest.mark.parametrize("name,interps", [
+    ("channel2d_17x17_L3", ("multilinear", "nearest1")),
+    ("incl2d_33x33_L4", ("multilinear",)),
+    ("channel2d_65x65_L3_adj", ("multilinear",)),
+])
+def test_hmh_vs_direct_report(name, interps):
+    _report(mi.workload(name), interps)
