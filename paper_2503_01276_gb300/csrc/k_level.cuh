@@ -39,7 +39,8 @@
 //       (because Ct M^-1 r = 0); p = z + (rho'/rho) p;
 //       q = A p; reduce p.q and Ct M^-1 q; alpha = rho' / p.q;
 //       lambda = alpha S^-1 Ct M^-1 q; delta += alpha p; r <- r - alpha q + Ct^T lambda.
-//     The sweep ends when sqrt(rho' / rho_first) < tol.
+//     The sweep ends when sqrt(rho' / rho_first) < max(tol, 0.3 rtol / ratio), ratio the
+//     refinement step's residual ratio: the last sweep stops once rtol is within reach.
 // Every warp evaluates the scalars and multipliers from the reduced sums itself. Keeping r
 // projected avoids the cancellation that otherwise pushes FP32 iterates off the constraint
 // set; the FP64 steps restore the constraints and the true residual.
@@ -511,6 +512,10 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
       if (!(ratio == ratio)) breakdown = true;
     }
     if (done || breakdown || step >= a.max_refine) break;
+    // the sweep's reduction target: the inner tolerance, relaxed once the refinement
+    // tolerance is within reach (0.3 rtol / ratio), so that the last sweep does not solve
+    // further than the refinement step needs
+    const T tol_s = T(fmax((double)a.tol, fmin(0.5, 0.3 * a.rtol / ratio)));
 
     // ================= inner PCG sweep =================
     C::sync();  // every rank has read red64; clear it and the inner buffers for reuse
@@ -620,7 +625,7 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
           const T rho_new = trz - T(2) * alpha * tzq + alpha * alpha * tqmq - lc;
           int stop = 0;
           if (bad) stop = 2;
-          else if (!(rho_new > T(a.tol) * T(a.tol) * rho0)) stop = 1;
+          else if (!(rho_new > tol_s * tol_s * rho0)) stop = 1;
           else if (it + 1 >= a.max_iter) stop = 1;
           const T beta = stop ? T(0) : rho_new / rho;
           rho = rho_new;
@@ -707,7 +712,7 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
         else if (it == 0) {
           rho0 = rho_new;
           if (!(rho0 > T(0))) stop = 1;
-        } else if (!(rho_new > T(a.tol) * T(a.tol) * rho0)) stop = 1;
+        } else if (!(rho_new > tol_s * tol_s * rho0)) stop = 1;
         if (!stop && it >= a.max_iter) stop = 1;
         if (stop) {
           if (stop == 2) breakdown = true;

@@ -739,8 +739,10 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
               S.flags[s] = (S.flags[s] & ~F_INNER) | F_DONE | F_BREAK;
             } else {
               S.rho[s] = rn;
-              if (!(rn >= (double)a.tol * (double)a.tol * S.rho_first[s]) ||
-                  it + 1 >= a.max_iter)
+              // the sweep's target: the inner tolerance, relaxed once the refinement
+              // tolerance is within reach (0.3 rtol / ratio)
+              const double ts = fmax((double)a.tol, fmin(0.5, 0.3 * a.rtol / S.ratio[s]));
+              if (!(rn >= ts * ts * S.rho_first[s]) || it + 1 >= a.max_iter)
                 S.flags[s] |= 8;  // last update of this sweep
             }
           }

@@ -53,6 +53,7 @@ cudaError_t launch_level2d_alt(const LevelArgs<float> &a, cudaStream_t st) {
     MCH_SHAPE(64, 6)
     MCH_SHAPE(64, 7)
     MCH_SHAPE(64, 8)
+    MCH_SHAPE(64, 9)
   }
   return launch_level2d_alt_big(a, st);
 }

@@ -21,10 +21,12 @@ cudaError_t launch_level2d_alt_big(const LevelArgs<float> &a, cudaStream_t st) {
     MCH_SHAPE(128, 5)
     MCH_SHAPE(128, 6)
     MCH_SHAPE(128, 7)
+    MCH_SHAPE(128, 8)
     MCH_SHAPE(256, 1)
     MCH_SHAPE(256, 2)
     MCH_SHAPE(256, 3)
     MCH_SHAPE(256, 4)
+    MCH_SHAPE(256, 5)
   }
   return cudaErrorInvalidValue;
 }

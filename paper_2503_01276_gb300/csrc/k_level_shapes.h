@@ -25,11 +25,12 @@ constexpr LevelShape kLevelShapes[] = {
     {64, 0, 8, 8, 1, 1, 4},   {64, 1, 4, 16, 1, 2, 1},  {64, 2, 4, 8, 2, 2, 1},
     {64, 3, 8, 4, 2, 1, 1},   {64, 4, 2, 8, 4, 4, 1},   {64, 5, 4, 4, 4, 3, 1},
     {64, 6, 8, 8, 1, 1, 1},   {64, 7, 4, 16, 1, 2, 4},  {64, 8, 8, 8, 1, 1, 2},
+    {64, 9, 8, 8, 1, 1, 6},
     {128, 0, 4, 16, 2, 1, 4}, {128, 1, 4, 8, 4, 1, 1},  {128, 2, 2, 8, 8, 3, 1},
     {128, 3, 4, 4, 8, 2, 1},  {128, 4, 4, 16, 2, 1, 1}, {128, 5, 4, 16, 2, 1, 6},
-    {128, 6, 4, 8, 4, 1, 4},  {128, 7, 4, 16, 2, 1, 8},
+    {128, 6, 4, 8, 4, 1, 4},  {128, 7, 4, 16, 2, 1, 8},  {128, 8, 4, 16, 2, 1, 12},
     {256, 0, 2, 16, 8, 1, 4}, {256, 1, 2, 16, 8, 1, 1}, {256, 2, 2, 16, 8, 1, 6},
-    {256, 3, 2, 16, 8, 1, 3}, {256, 4, 2, 16, 8, 1, 8},
+    {256, 3, 2, 16, 8, 1, 3}, {256, 4, 2, 16, 8, 1, 8},  {256, 5, 2, 16, 8, 1, 12},
     // grids with an odd number of sub-blocks per side (P = 3: m = 8, 16, 32)
     {24, 0, 12, 2, 1, 3, 2},  {48, 0, 6, 8, 1, 2, 2},   {96, 0, 4, 8, 3, 1, 4},
 };

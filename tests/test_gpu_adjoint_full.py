@@ -146,10 +146,11 @@ def _descendants(pl):
 def test_central_differences_64_elements(case):
     """Relative step 1e-4 (the O(h^2) truncation is ~1e-8 of the derivative; with a step of
     1e-6 the solves' own run-to-run noise is above the signal of elements that carry little
-    energy). Only the perturbed point and its descendants are re-read. The allowance for
-    that noise is 1e-12 of the affected weighted coefficients sum |W||E| (two solves of the
-    same medium at rtol 1e-11 agree much closer than that); at least 24 of the 64 elements
-    must have an allowance below 1e-3 of their derivative."""
+    energy). Only the perturbed point and its descendants are re-read. The solves run at
+    rtol 1e-12; a child's coefficients inherit about rtol of its parents' cell functions, so
+    the allowance for the noise of the difference of two solves is 2 rtol of the affected
+    weighted coefficients sum |W||E|; at least 24 of the 64 elements must have an allowance
+    below 1e-3 of their derivative."""
     pl, med, W, _ = case
     h = 1e-4
     closure = _descendants(pl)
@@ -165,7 +166,8 @@ def test_central_differences_64_elements(case):
                 if lab[p, e] == want:
                     break
             picks.append((lv, p, e))
-    s = mch.Solver.from_workload(WL, rtol=RTOL)
+    rtol_fd = 1e-12
+    s = mch.Solver.from_workload(WL, rtol=rtol_fd)
     md = _dev_media(med)
     _solve(s, md)
     g = _grad(s, W)
@@ -193,7 +195,7 @@ def test_central_differences_64_elements(case):
         kap = med[lv - 1][0][p, e]
         fd = dL / (2 * h * kap)
         ad = g[lv - 1][p, e]
-        noise = 1e-12 * scale / (2 * h * kap)
+        noise = 2 * rtol_fd * scale / (2 * h * kap)
         rel.append((lv, int(med[lv - 1][1][p, e]), fd, ad, noise))
         assert abs(fd - ad) <= 1e-5 * abs(ad) + noise, (lv, p, e, fd, ad, noise)
     informative = sum(1 for (_, _, fd, ad, nz) in rel if nz < 1e-3 * abs(ad))
