@@ -377,7 +377,7 @@ class GpuRun:
             for lev, v in enumerate(tiles, start=1):
                 self.s.set_variant(lev, v)
             self.tiles = list(tiles)
-        elif autotune and wl.dim == 2 and wl.precision == "mixed":
+        elif autotune and wl.dim == 2:
             for lev in range(1, self.L + 1):
                 v, _ = self.s.autotune_level(lev, *self.med_dev[lev - 1])
                 self.tiles.append(v)
@@ -682,9 +682,16 @@ def main():
     ap.add_argument("--rtol", type=float, default=RTOL,
                     help="refinement tolerance of the solves (the accuracy the metric names "
                          "is checked against the oracle)")
+    ap.add_argument("--inner-tol", type=float, default=0.0,
+                    help="per-sweep reduction of the inner PCG (0: the library default)")
     ap.add_argument("--tiles", default=None,
                     help="comma-separated launch shapes per level instead of autotuning "
                          "(fixed launch counts, for profiling)")
+    ap.add_argument("--macro-n", type=int, default=None,
+                    help="reduced copy of the workload: macropoints per axis (with --strides; "
+                         "for profiling a small case)")
+    ap.add_argument("--strides", default=None,
+                    help="comma-separated level strides of the reduced copy")
     ap.add_argument("--cpu-leg", default=None, help=argparse.SUPPRESS)
     args = ap.parse_args()
     if args.cpu_leg is not None:
@@ -708,10 +715,14 @@ def main():
     stream = torch.cuda.current_stream()
     wl = mi.workload(args.workload, precision=args.precision,
                      seed=mi.workload(args.workload).seed + rank)
+    if args.macro_n is not None:
+        strides = tuple(int(v) for v in args.strides.split(",")) if args.strides else (1,)
+        wl = mi.small_workload(args.workload, n_fine=wl.n_fine, macro_n=args.macro_n,
+                               strides=strides, precision=args.precision, seed=wl.seed)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     tiles = [int(v) for v in args.tiles.split(",")] if args.tiles else None
 
-    g = GpuRun(wl, dev, stream, tiles=tiles, rtol=args.rtol)
+    g = GpuRun(wl, dev, stream, tiles=tiles, rtol=args.rtol, inner_tol=args.inner_tol)
     t = g.timed(args.steps, args.warmup, flush, dist if world > 1 else None, world)
     t_total = max_over_ranks(float(np.sum(t["step_ms"])) / 1e3, dist if world > 1 else None, dev)
     value = whole_job_rate(g.rhs_per_step, world, args.steps, t_total)

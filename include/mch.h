@@ -82,7 +82,8 @@ typedef struct {
                                child's coefficients inherit the error of its parents'
                                functions to first order (about rtol); a level's own
                                coefficients are quadratic in its error */
-  double inner_tol;         /* per-sweep PCG reduction of the same norm (0 -> 1e-4)         */
+  double inner_tol;         /* per-sweep PCG reduction of the same norm (0 -> 1e-5 in 2D,
+                               1e-4 in 3D)                                                  */
   int max_iter;             /* PCG iterations per sweep (0 -> 4 n_level + 50)               */
   int max_refine;           /* refinement sweeps (0 -> 6)                                   */
   int keep_parents;         /* 1: keep every level's cell functions on the level-1 grid

@@ -70,6 +70,7 @@ struct mch_handle {
   std::vector<Level> lv;
   // scratch shared by the levels (solved one after another)
   double *yfine = nullptr, *yc = nullptr;
+  size_t yfine_cap = 0;           // doubles in yfine
   double *bnorm = nullptr;  // [unit] b'M^-1 b of the current correction or adjoint problem
   // oversampling (o > 0): A_1 I with kappa masked to R_p (level-1 grid), P^T of it (level
   // grid), and the masked level kappa
@@ -434,9 +435,8 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
       (d.precision != MCH_FP64 && d.precision != MCH_MIXED) || d.rtol < 0 || d.inner_tol < 0 ||
       d.max_iter < 0 || d.max_refine < 0 || d.point_batch < 0)
     return MCH_ERR_ARG;
-  // oversampling: 2D only, at least one period in the integration region
+  // oversampling: at least one period in the integration region
   if (d.overs < 0 || d.periods - 2 * d.overs < 1) return MCH_ERR_ARG;
-  if (d.overs != 0 && d.dim != 2) return MCH_ERR_UNSUPPORTED;
   const int nq = d.dim == 3 ? d.periods * d.periods * d.periods : d.periods * d.periods;
   const int nc = d.n_cont * nq;
   if (nc > (d.dim == 3 ? MCH_MAX_NC3 : MCH_MAX_NC)) return MCH_ERR_UNSUPPORTED;
@@ -448,7 +448,9 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
   h->strides.assign(d.level_stride, d.level_stride + d.n_levels);
   h->d.level_stride = h->strides.data();
   if (h->d.rtol == 0) h->d.rtol = 1e-8;
-  if (h->d.inner_tol == 0) h->d.inner_tol = 1e-4;
+  // default per-sweep reduction: 1e-5 in 2D (the Chebyshev-preconditioned on-chip sweeps
+  // reach it and save a refinement step), 1e-4 in 3D (the streaming sweeps pay per iteration)
+  if (h->d.inner_tol == 0) h->d.inner_tol = d.dim == 3 ? 1e-4 : 1e-5;
   if (h->d.max_refine == 0) h->d.max_refine = 6;
   h->st = (cudaStream_t)cuda_stream;
   h->R = d.n_cont * (1 + d.dim);
@@ -553,6 +555,7 @@ mch_status mch_create(const mch_desc *desc, void *cuda_stream, mch_handle **out)
     ALLOC(h->bnorm, max_units);
   }
   if (max_fine) ALLOC(h->yfine, max_fine);
+  h->yfine_cap = max_fine;
   if (d.overs > 0) {
     size_t max_el = 0;
     for (const Level &L : h->lv) max_el = std::max(max_el, (size_t)L.npts * elems(d.dim, L.n));
@@ -725,7 +728,7 @@ mch_status solve_range(mch_handle *h, int level, int p0, int p1, const double *k
                            L.Sinv64 + p0 * nc * nc, L.minv + p0 * L.nv, g + p0 * nc * R, bb,
                            L.x + u0 * L.nv, L.iters + u0, L.sweeps + u0, L.ratio + u0,
                            L.ustat + u0, (float)d.inner_tol, max_iter, d.rtol, d.max_refine, lam,
-                           bvec ? h->bnorm + u0 : nullptr};
+                           bvec ? h->bnorm + u0 : nullptr, L0.variant};
       CK(launch_level2d<double>(la, st), "level fp64");
     } else {
       LevelArgs<float> la{cn, R, L.n, P, N, nc, L.nv, ilog2(L.n / P), ilog2(P),
@@ -746,7 +749,7 @@ mch_status solve_range(mch_handle *h, int level, int p0, int p1, const double *k
   // R_p: |R_p| E = K_I,R + sym(Xi^T (A_n,R Xi + 2 P^T A_1,R I))
   ApplyArgs ac{(int)np, R, L.n, 1, L.nv, L.kappa, L.x, bvec, -2.0, h->yc};
   if (ovs) {
-    CK(launch_mask_region2d((int)np, L.n, P, d.overs, L.kappa, h->kapR, st), "mask kappa");
+    CK(launch_mask_region(d.dim, (int)np, L.n, P, d.overs, L.kappa, h->kapR, st), "mask kappa");
     ++h->launches;
     ac.kappa = h->kapR;
     ac.b = li > 0 ? h->cR : nullptr;
@@ -891,16 +894,28 @@ mch_status mch_set_cell_functions(mch_handle *h, int level, int p0, int p1, cons
   double *dst = L.phi + (size_t)p0 * h->R * L.nvf;
   const bool dev = is_device_ptr(phi);
   if (!dev) h->h2d += (long long)(rows * len * sizeof(double));
-  if (h->ffs) {
-    // FP64 -> float-float planes, through the level-1-grid scratch for host sources
-    const double *src = phi;
-    if (!dev) {
-      CK(cudaMemcpyAsync(h->yfine, phi, rows * len * sizeof(double), cudaMemcpyHostToDevice,
-                         h->st),
-         "stage cell functions");
-      src = h->yfine;
+  if (h->ffs && dev) {
+    CK(launch_to_ff((int)rows, phi, (int)len, dst, L.nvf, (int)len, h->st), "convert phi");
+  } else if (h->ffs) {
+    // FP64 -> float-float planes, host sources staged through the level-1-grid scratch (or a
+    // temporary buffer when the hierarchy has none) in chunks of whole vectors
+    double *buf = h->yfine, *tmp = nullptr;
+    size_t cap = h->yfine_cap / len;
+    if (cap == 0) {
+      CK(dalloc(h, &tmp, len), "cell functions buffer");
+      buf = tmp;
+      cap = 1;
     }
-    CK(launch_to_ff((int)rows, src, (int)len, dst, L.nvf, (int)len, h->st), "convert phi");
+    for (size_t r0 = 0; r0 < rows; r0 += cap) {
+      const size_t cnt = std::min(cap, rows - r0);
+      CK(cudaMemcpyAsync(buf, phi + r0 * len, cnt * len * sizeof(double),
+                         cudaMemcpyHostToDevice, h->st),
+         "stage cell functions");
+      CK(launch_to_ff((int)cnt, buf, (int)len, dst + r0 * L.nvf, L.nvf, (int)len, h->st),
+         "convert phi");
+      CK(cudaStreamSynchronize(h->st), "sync");
+    }
+    if (tmp) dfree(h, tmp);
   } else {
     CK(cudaMemcpy2DAsync(dst, (size_t)L.nvf * sizeof(double), phi, len * sizeof(double),
                          len * sizeof(double), rows,
@@ -1351,7 +1366,8 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
                h->slots, inv_vol, 1.0 / rho_pow(h, L.rho), h->Wd, L.phi,
                seeds ? h->yc : nullptr, L.lam, seeds ? h->lamadj : nullptr, L.kappa, L.labels,
                L.V, h->psi1, h->psi2, h->dk, L.par_V, L.par_w, h->ffs ? 1 : 0, d.overs};
-    if (d.overs > 0) CK(launch_adj_own2d(aa, st), "adjoint own term");
+    if (d.overs > 0)
+      CK(d3 ? launch_adj_own3d(aa, hf, st) : launch_adj_own2d(aa, st), "adjoint own term");
     if (seeds) {
       // adjoint constrained solve with right-hand side P^T V and zero targets
       if (L.rho > 1) {
@@ -1372,7 +1388,7 @@ mch_status mch_backward(mch_handle *h, const double *const *dL_dE, double *const
                              L.labels, L.Sinv64, L.Sinv64, L.minv, h->gzero, L.b, h->yc,
                              h->bw_iters, h->bw_sweeps, h->bw_ratio, h->bw_status,
                              (float)d.inner_tol, max_iter, d.rtol, d.max_refine, h->lamadj,
-                             h->bnorm};
+                             h->bnorm, L.variant};
         CK(launch_level2d<double>(la, st), "adjoint fp64");
       } else {
         LevelArgs<float> la{(int)np, R, L.n, P, N, nc, L.nv, ilog2(L.n / P), ilog2(P), L.kappa,

@@ -10,7 +10,10 @@
 // Backward (see k_adjoint.cu for the 2D form and the derivation): Psi' = sum_r What_rs Phi_r
 // - P mu_s, Psi = 1/2 sum_r What_rs Phi_r - P mu_s; dL/dkappa_E = sum_{fine e in E}
 // h_f Psi_s|e^T Khat Phi_s|e; U_r = V_r + A_1 Psi'_r + rho^-3 Ct_1^T sigma_r pushed to the
-// parents.
+// parents. With oversampling (E over R_p, the central (P - 2 o)^3 periods) E is not
+// stationary in the cell functions: as in 2D, the level's own term sum_s What_rs A_{1,R}
+// Phi_s is an adjoint source of every level (k_adj_own3d), the envelope terms are dropped,
+// and the direct term counts only the elements inside R_p.
 #include <type_traits>
 
 #include "ff.cuh"
@@ -182,11 +185,31 @@ __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double
         }
       }
     };
+    // oversampling: the same stencil with kappa zero outside R_p (period index of each
+    // adjacent fine element)
+    const int o = a.overs;
+    auto in_r = [&](int ex, int ey, int ez) {
+      const int px = ex >> a.lgmf, py = ey >> a.lgmf, pz = ez >> a.lgmf;
+      return px >= o && px < P - o && py >= o && py < P - o && pz >= o && pz < P - o;
+    };
     for (int kz = 1; kz < nf; ++kz) {
       load_v(v[2], kz + 1);
       load_k(kk[1], up, kz);
       const V val = v[1][1][1];
       S::st(a.y, unit, a.nvf, (int)(base + W2 * kz), hv * q1_apply3d_v<V>(v, kk, third, twelfth));
+      if (a.yR) {
+        V kr[2][2][2];
+#pragma unroll
+        for (int sz = 0; sz < 2; ++sz)
+#pragma unroll
+          for (int sy = 0; sy < 2; ++sy)
+#pragma unroll
+            for (int sx = 0; sx < 2; ++sx)
+              kr[sz][sy][sx] = in_r(kx - 1 + sx, ky - 1 + sy, kz - 1 + sz) ? kk[sz][sy][sx]
+                                                                           : S::zero();
+        S::st(a.yR, unit, a.nvf, (int)(base + W2 * kz),
+              hv * q1_apply3d_v<V>(v, kr, third, twelfth));
+      }
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
@@ -323,8 +346,9 @@ __global__ void __launch_bounds__(F3_THREADS) k_adj_combine3d(AdjArgs a) {
 #pragma unroll
   for (int s = 0; s < R; ++s) {
     double x = 0.0;
+    if (!a.overs)
 #pragma unroll
-    for (int r = 0; r < R; ++r) x += wh[r * R + s] * phi[r];
+      for (int r = 0; r < R; ++r) x += wh[r * R + s] * phi[r];
     double pm = 0.0;
     if (a.mu) {
       const double *m = a.mu + ((size_t)pt * R + s) * a.nvc + c0;
@@ -349,6 +373,41 @@ __global__ void __launch_bounds__(F3_THREADS) k_adj_grad3d(AdjArgs a, double hf)
   const int Ex = E % ncg, Ey = (E / ncg) % ncg, Ez = E / (ncg * ncg);
   const size_t sy = Wf, sz = (size_t)Wf * Wf;
   double g = 0.0;
+  if (a.overs) {
+    // direct term sum_rs W_rs Phi_r^T Khat Phi_s / |R_p| on the elements inside R_p (R_p is a
+    // union of level-n elements: test one fine element's period)
+    const int P = a.P, o = a.overs;
+    const int px = (Ex * rho) >> a.lgmf, py = (Ey * rho) >> a.lgmf, pz = (Ez * rho) >> a.lgmf;
+    if (px >= o && px < P - o && py >= o && py < P - o && pz >= o && pz < P - o) {
+      const double *Wp = a.W + (size_t)pt * R * R;
+      const size_t off[8] = {0, 1, sy, sy + 1, sz, sz + 1, sz + sy, sz + sy + 1};
+      for (int kz = 0; kz < rho; ++kz)
+        for (int jy = 0; jy < rho; ++jy)
+          for (int ix = 0; ix < rho; ++ix) {
+            const size_t k0 = (Ex * rho + ix) + sy * (Ey * rho + jy) + sz * (Ez * rho + kz);
+            for (int s = 0; s < R; ++s) {
+              double kp[8];
+              {
+                double p[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) p[c] = phi3(a, (size_t)pt * R + s, k0 + off[c]);
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                  kp[c] = p[c] * (1.0 / 3.0) -
+                          (p[c ^ 3] + p[c ^ 5] + p[c ^ 6] + p[c ^ 7]) * (1.0 / 12.0);
+              }
+              for (int r = 0; r < R; ++r) {
+                const double w = Wp[r * R + s];
+                if (w == 0.0) continue;
+                double e = 0.0;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) e += phi3(a, (size_t)pt * R + r, k0 + off[c]) * kp[c];
+                g += w * a.inv_vol * e;
+              }
+            }
+          }
+    }
+  }
   for (int kz = 0; kz < rho; ++kz)
     for (int jy = 0; jy < rho; ++jy)
       for (int ix = 0; ix < rho; ++ix) {
@@ -386,8 +445,9 @@ __global__ void __launch_bounds__(F3_THREADS) k_adj_seed3d(AdjArgs a, double hf)
   for (int b = threadIdx.x; b < nc; b += F3_THREADS) {
     double sgm = 0.0;
     const double *Wp = a.W + (size_t)pt * R * R;
-    for (int s = 0; s < R; ++s)
-      sgm += (Wp[r * R + s] + Wp[s * R + r]) * a.inv_vol * a.lam[((size_t)pt * R + s) * nc + b];
+    if (!a.overs)
+      for (int s = 0; s < R; ++s)
+        sgm += (Wp[r * R + s] + Wp[s * R + r]) * a.inv_vol * a.lam[((size_t)pt * R + s) * nc + b];
     if (a.lamadj) sgm -= a.lamadj[((size_t)pt * R + r) * nc + b];
     sig[b] = sgm * a.inv_rho2;
   }
@@ -429,7 +489,69 @@ __global__ void __launch_bounds__(F3_THREADS) k_adj_seed3d(AdjArgs a, double hf)
   }
 }
 
+// Oversampling: V_r += sum_s What_rs A_{1,R} Phi_s at the interior fine nodes, with kappa
+// zero on the fine elements outside R_p.
+template <int R>
+__global__ void __launch_bounds__(F3_THREADS) k_adj_own3d(AdjArgs a, double hf) {
+  const int pt = blockIdx.y;
+  const int nf = a.nf, Wf = nf + 1, lgr = a.lgr, ncg = nf >> lgr;
+  const int k = blockIdx.x * F3_THREADS + threadIdx.x;
+  if (k >= Wf * Wf * Wf) return;
+  const int fx = k % Wf, fy = (k / Wf) % Wf, fz = k / (Wf * Wf);
+  if (fx == 0 || fy == 0 || fz == 0 || fx == nf || fy == nf || fz == nf) return;
+  const int P = a.P, o = a.overs;
+  const double *kc = a.kappa_c + (size_t)pt * ncg * ncg * ncg;
+  double kk[2][2][2];
+#pragma unroll
+  for (int sz = 0; sz < 2; ++sz)
+#pragma unroll
+    for (int sy = 0; sy < 2; ++sy)
+#pragma unroll
+      for (int sx = 0; sx < 2; ++sx) {
+        const int ex = fx - 1 + sx, ey = fy - 1 + sy, ez = fz - 1 + sz;
+        const int px = ex >> a.lgmf, py = ey >> a.lgmf, pz = ez >> a.lgmf;
+        const bool in = px >= o && px < P - o && py >= o && py < P - o && pz >= o && pz < P - o;
+        kk[sz][sy][sx] = in ? kc[cidx(ex >> lgr, ey >> lgr, ez >> lgr, ncg)] : 0.0;
+      }
+  const size_t W2 = (size_t)Wf * Wf;
+  double y[R];
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    double v[3][3][3];
+    const size_t vs = (size_t)pt * R + s;
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx)
+          v[dz][dy][dx] = phi3(a, vs, k + (dx - 1) + Wf * (dy - 1) + W2 * (dz - 1));
+    y[s] = hf * q1_apply3d<double>(v, kk);
+  }
+  const double *Wp = a.W + (size_t)pt * R * R;
+  double *V = const_cast<double *>(a.V);
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    double u = 0.0;
+#pragma unroll
+    for (int s = 0; s < R; ++s) u += (Wp[r * R + s] + Wp[s * R + r]) * a.inv_vol * y[s];
+    V[((size_t)pt * R + r) * a.nvf + k] += u;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_adj_own3d(const AdjArgs &a, double hf, cudaStream_t st) {
+  const int Wf = a.nf + 1;
+  dim3 grid((Wf * Wf * Wf + F3_THREADS - 1) / F3_THREADS, a.npts);
+  switch (a.R) {
+    case 4: k_adj_own3d<4><<<grid, F3_THREADS, 0, st>>>(a, hf); break;
+    case 8: k_adj_own3d<8><<<grid, F3_THREADS, 0, st>>>(a, hf); break;
+    case 12: k_adj_own3d<12><<<grid, F3_THREADS, 0, st>>>(a, hf); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_apply3d(const ApplyArgs &a, double h, cudaStream_t st) {
   dim3 grid((a.nv + F3_THREADS - 1) / F3_THREADS, a.npts * a.R);

@@ -63,21 +63,27 @@ __global__ void __launch_bounds__(256) k_bnorm(int R, int nv, const double *b, c
 
 namespace {
 
-__global__ void k_mask_region2d(int n, int P, int overs, const double *kappa, double *out) {
+__global__ void k_mask_region(int dim, int n, int P, int overs, const double *kappa,
+                              double *out) {
   const int pt = blockIdx.y;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n * n) return;
-  const int m = n / P, px = (e % n) / m, py = (e / n) / m;
-  const bool in = px >= overs && px < P - overs && py >= overs && py < P - overs;
-  out[(size_t)pt * n * n + e] = in ? kappa[(size_t)pt * n * n + e] : 0.0;
+  const long long ne = dim == 3 ? (long long)n * n * n : (long long)n * n;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const int m = n / P;
+  const int px = (int)(e % n) / m, py = (int)((e / n) % n) / m;
+  const int pz = dim == 3 ? (int)(e / ((long long)n * n)) / m : overs;
+  const bool in = px >= overs && px < P - overs && py >= overs && py < P - overs &&
+                  pz >= overs && pz < P - overs;
+  out[(size_t)pt * ne + e] = in ? kappa[(size_t)pt * ne + e] : 0.0;
 }
 
 }  // namespace
 
-cudaError_t launch_mask_region2d(int npts, int n, int P, int overs, const double *kappa,
-                                 double *out, cudaStream_t st) {
-  dim3 grid((n * n + 255) / 256, npts);
-  k_mask_region2d<<<grid, 256, 0, st>>>(n, P, overs, kappa, out);
+cudaError_t launch_mask_region(int dim, int npts, int n, int P, int overs, const double *kappa,
+                               double *out, cudaStream_t st) {
+  const long long ne = dim == 3 ? (long long)n * n * n : (long long)n * n;
+  dim3 grid((unsigned)((ne + 255) / 256), npts);
+  k_mask_region<<<grid, 256, 0, st>>>(dim, n, P, overs, kappa, out);
   return cudaGetLastError();
 }
 

@@ -9,22 +9,24 @@ namespace mch {
 cudaError_t launch_level2d_alt_big(const LevelArgs<float> &a, cudaStream_t st);
 
 int level2d_variant_count(int n, bool fp64) {
-  if (fp64) return 1;
   int c = 0;
-  for (const LevelShape &s : kLevelShapes) c += s.n == n;
-  return c;
+  if (fp64) {
+    for (const LevelShape &s : kLevelShapes64) c += s.n == n;
+  } else {
+    for (const LevelShape &s : kLevelShapes) c += s.n == n;
+  }
+  return c > 0 ? c : 1;
 }
 
 bool level2d_variant_ok(int n, int P, bool fp64, int v) {
   if (v == 0) return level2d_supported(n, P, fp64);
-  if (fp64 || !level2d_supported(n, P, fp64)) return false;
-  const LevelShape *s = find_level_shape(n, v);
+  if (!level2d_supported(n, P, fp64)) return false;
+  const LevelShape *s = find_level_shape(n, v, fp64);
   return s && (n / P) % s->rpt == 0;
 }
 
 int level2d_cheb_steps(int n, bool fp64, int v) {
-  if (fp64) return 1;
-  const LevelShape *s = find_level_shape(n, v);
+  const LevelShape *s = find_level_shape(n, v, fp64);
   return s ? s->nch : 1;
 }
 

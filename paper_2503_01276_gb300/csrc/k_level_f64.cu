@@ -1,5 +1,7 @@
-// FP64-inner instantiations of the persistent level kernel (the plain FP64 mode).
+// FP64-inner instantiations of the persistent level kernel (the plain FP64 mode): every
+// shape of the FP64 table in k_level_shapes.h.
 #include "k_level.cuh"
+#include "k_level_shapes.h"
 
 namespace mch {
 
@@ -23,16 +25,29 @@ bool level2d_supported(int n, int P, bool fp64) {
   return m % rpt == 0;
 }
 
+#define MCH_SHAPE64(N_, V_)                                                                 \
+  case N_ * 16 + V_: {                                                                      \
+    constexpr LevelShape s = *find_level_shape(N_, V_, true);                               \
+    return launch_level_nc<double, N_, s.rg, s.rpt, s.cl, s.minb, s.nch>(a, st);            \
+  }
+
 template <>
 cudaError_t launch_level2d<double>(const LevelArgs<double> &a, cudaStream_t st) {
-  switch (a.n) {
-    case 16: return launch_level_nc<double, 16, 16, 1, 1, 2>(a, st);
-    case 32: return launch_level_nc<double, 32, 8, 4, 1, 2>(a, st);
-    case 64: return launch_level_nc<double, 64, 8, 4, 2, 1>(a, st);
-    case 128: return launch_level_nc<double, 128, 4, 8, 4, 1>(a, st);
-    case 24: return launch_level_nc<double, 24, 12, 2, 1, 2>(a, st);
-    case 48: return launch_level_nc<double, 48, 6, 8, 1, 1>(a, st);
-    case 96: return launch_level_nc<double, 96, 4, 8, 3, 1>(a, st);
+  switch (a.n * 16 + a.variant) {
+    MCH_SHAPE64(16, 0)
+    MCH_SHAPE64(16, 1)
+    MCH_SHAPE64(32, 0)
+    MCH_SHAPE64(32, 1)
+    MCH_SHAPE64(32, 2)
+    MCH_SHAPE64(64, 0)
+    MCH_SHAPE64(64, 1)
+    MCH_SHAPE64(64, 2)
+    MCH_SHAPE64(128, 0)
+    MCH_SHAPE64(128, 1)
+    MCH_SHAPE64(128, 2)
+    MCH_SHAPE64(24, 0)
+    MCH_SHAPE64(48, 0)
+    MCH_SHAPE64(96, 0)
   }
   return cudaErrorInvalidValue;
 }

@@ -35,7 +35,22 @@ constexpr LevelShape kLevelShapes[] = {
     {24, 0, 12, 2, 1, 3, 2},  {48, 0, 6, 8, 1, 2, 2},   {96, 0, 4, 8, 3, 1, 4},
 };
 
-constexpr const LevelShape *find_level_shape(int n, int v) {
+// Shapes of the FP64-inner kernel (the plain FP64 mode): index 0 is the default of
+// k_level_f64.cu; the others (k_level_f64.cu) add Chebyshev steps to the same tiles.
+constexpr LevelShape kLevelShapes64[] = {
+    {16, 0, 16, 1, 1, 2, 1},  {16, 1, 16, 1, 1, 2, 2},
+    {32, 0, 8, 4, 1, 2, 1},   {32, 1, 8, 4, 1, 2, 2},  {32, 2, 8, 4, 1, 2, 4},
+    {64, 0, 8, 4, 2, 1, 1},   {64, 1, 8, 4, 2, 1, 4},  {64, 2, 8, 4, 2, 1, 6},
+    {128, 0, 4, 8, 4, 1, 1},  {128, 1, 4, 8, 4, 1, 4}, {128, 2, 4, 8, 4, 1, 8},
+    {24, 0, 12, 2, 1, 2, 1},  {48, 0, 6, 8, 1, 1, 1},  {96, 0, 4, 8, 3, 1, 1},
+};
+
+constexpr const LevelShape *find_level_shape(int n, int v, bool fp64 = false) {
+  if (fp64) {
+    for (const LevelShape &s : kLevelShapes64)
+      if (s.n == n && s.v == v) return &s;
+    return nullptr;
+  }
   for (const LevelShape &s : kLevelShapes)
     if (s.n == n && s.v == v) return &s;
   return nullptr;

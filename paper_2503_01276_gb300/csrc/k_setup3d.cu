@@ -153,16 +153,32 @@ __global__ void __launch_bounds__(S3P_THREADS) k_setup3d_point(SetupArgs a) {
   for (int i = tid; i < 4 * nc; i += S3P_THREADS) bs[i] = a.bacc[(size_t)pt * nc * 4 + i];
   __syncthreads();
 
+  // centroids c_mj over the integration region R_p (the central (P - 2 overs)^3 periods;
+  // the whole RVE when the continuum is absent there, or when overs = 0)
   if (tid < N) {
-    double c = 0, x = 0, y = 0, z = 0;
+    double c = 0, x = 0, y = 0, z = 0, ca = 0, xa = 0, ya = 0, za = 0;
+    const int o = a.overs;
     for (int q = 0; q < nq; ++q) {
       const int b = tid * nq + q;
-      c += bs[4 * b];
-      x += bs[4 * b + 1];
-      y += bs[4 * b + 2];
-      z += bs[4 * b + 3];
+      const int qx = q % P, qy = (q / P) % P, qz = q / (P * P);
+      ca += bs[4 * b];
+      xa += bs[4 * b + 1];
+      ya += bs[4 * b + 2];
+      za += bs[4 * b + 3];
+      if (qx >= o && qx < P - o && qy >= o && qy < P - o && qz >= o && qz < P - o) {
+        c += bs[4 * b];
+        x += bs[4 * b + 1];
+        y += bs[4 * b + 2];
+        z += bs[4 * b + 3];
+      }
     }
-    if (c == 0.0) atomicOr(&flags, 8);
+    if (ca == 0.0) atomicOr(&flags, 8);
+    if (c == 0.0) {
+      c = ca;
+      x = xa;
+      y = ya;
+      z = za;
+    }
     cen[3 * tid] = c > 0 ? x / c : 0.0;
     cen[3 * tid + 1] = c > 0 ? y / c : 0.0;
     cen[3 * tid + 2] = c > 0 ? z / c : 0.0;

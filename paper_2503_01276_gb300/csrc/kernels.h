@@ -76,9 +76,9 @@ struct ApplyArgs {
 };
 cudaError_t launch_apply2d(const ApplyArgs &a, cudaStream_t st);
 
-// out[pt][e] = kappa[pt][e] on elements of the central (P - 2 overs)^2 periods, else 0 (2D).
-cudaError_t launch_mask_region2d(int npts, int n, int P, int overs, const double *kappa,
-                                 double *out, cudaStream_t st);
+// out[pt][e] = kappa[pt][e] on elements of the central (P - 2 overs)^d periods, else 0.
+cudaError_t launch_mask_region(int dim, int npts, int n, int P, int overs, const double *kappa,
+                               double *out, cudaStream_t st);
 
 // out[unit] = sum_k b[unit][k]^2 minv[pt][k] over nv entries (units = npts * R), FP64.
 cudaError_t launch_bnorm(int npts, int R, int nv, const double *b, const double *minv,
@@ -236,5 +236,7 @@ cudaError_t launch_adj_own2d(const AdjArgs &a, cudaStream_t st);
 cudaError_t launch_adj_combine3d(const AdjArgs &a, cudaStream_t st);
 cudaError_t launch_adj_grad3d(const AdjArgs &a, double hf, cudaStream_t st);
 cudaError_t launch_adj_seed3d(const AdjArgs &a, double hf, cudaStream_t st);
+// V[pt][r] += sum_s What_rs A_{1,R} Phi_s on the level-1 grid (3D oversampling only).
+cudaError_t launch_adj_own3d(const AdjArgs &a, double hf, cudaStream_t st);
 
 }  // namespace mch

@@ -69,8 +69,8 @@ def test_descriptor_validation_without_gpu(mch):
     assert lib.mch_create(ctypes.byref(bad), None, ctypes.byref(h)) == 1
     ov = mch.desc_from_workload(wl, overs=2)          # no period left in R_p (P = 4)
     assert lib.mch_create(ctypes.byref(ov), None, ctypes.byref(h)) == 1
-    ov = mch.desc_from_workload(mi.workload("channel3d_9x9x9_L3"), overs=1)
-    assert lib.mch_create(ctypes.byref(ov), None, ctypes.byref(h)) == 8
+    ov = mch.desc_from_workload(mi.workload("channel3d_9x9x9_L3"), overs=2)   # 3D, none left
+    assert lib.mch_create(ctypes.byref(ov), None, ctypes.byref(h)) == 1
     # 3 sub-blocks per side do not divide the 128-element grid: refused, not mis-solved
     # (grids 96 / 48 / 24 with 3 sub-blocks run; the kernels need a power-of-two number of
     # elements per sub-block)

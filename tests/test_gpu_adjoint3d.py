@@ -1,5 +1,6 @@
 """3D backward pass against the oracle's gradient and the Euler identity (grids 16/8,
-2x2x2 periods, mixed and FP64, rtol 1e-11)."""
+2x2x2 periods, mixed and FP64, rtol 1e-11; and with oversampling, o = 1 of 4x4x4 periods,
+where the level's own term is an adjoint source)."""
 import numpy as np
 import pytest
 
@@ -15,10 +16,15 @@ if not torch.cuda.is_available():
 import paper_2503_01276_gb300 as mch  # noqa: E402
 
 
-@pytest.mark.parametrize("precision", ["mixed", "fp64"])
-def test_3d_gradient_vs_oracle(precision):
-    wl = mi.small_workload("channel3d_9x9x9_L3", n_fine=16, macro_n=3, strides=(2, 1),
-                           periods=2, precision=precision)
+@pytest.mark.parametrize("precision,overs", [("mixed", 0), ("fp64", 0), ("mixed", 1),
+                                             ("fp64", 1)])
+def test_3d_gradient_vs_oracle(precision, overs):
+    if overs:
+        wl = mi.small_workload("channel3d_9x9x9_L3", n_fine=16, macro_n=3, strides=(2, 1),
+                               periods=4, eta=1, overs=1, precision=precision)
+    else:
+        wl = mi.small_workload("channel3d_9x9x9_L3", n_fine=16, macro_n=3, strides=(2, 1),
+                               periods=2, precision=precision)
     pl = plan.level_plan(wl)
     med = [mi.media(wl, l["points"], wl.n_level(k + 1)) for k, l in enumerate(pl)]
     rng = np.random.default_rng(7)

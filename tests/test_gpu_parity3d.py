@@ -71,6 +71,19 @@ def test_3d_hierarchy_small(n_fine, macro, strides, periods, eta, precision):
         assert (np.abs(phi - ref) / scale).max() < 1e-9, lev
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_3d_oversampling(precision):
+    """R_p = the central 2x2x2 of the 4x4x4 periods (o = 1): centroids and E over R_p, every
+    level of a two-level hierarchy (eta = 1, 16^3) against the oracle."""
+    wl = mi.small_workload(NAME, n_fine=16, macro_n=3, strides=(2, 1), periods=4, eta=1,
+                           overs=1, precision=precision)
+    s, Eg = _run_gpu(wl, rtol=1e-11)
+    Eo = _run_oracle(wl)
+    for lev in range(wl.n_levels):
+        err = block_rel_err(Eg[lev], Eo[lev]["E"], wl.n_cont, wl.dim)
+        assert err < 1e-9, (lev + 1, err)
+
+
 def test_3d_single_level_32_against_oracle():
     """One level, 3x3x3 macropoints on 32^3 RVEs with 4x4x4 periods (the size of the 9^3
     workload's second level): two points element by element against the oracle."""

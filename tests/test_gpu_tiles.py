@@ -1,12 +1,14 @@
-"""Launch shapes of the 2D mixed-precision level solve and the autotuner.
+"""Launch shapes of the 2D level solve (mixed precision and FP64) and the autotuner.
 
-Every valid shape of every grid size must give the default shape's effective coefficients
-(to the solver tolerance: rtol = 1e-11, compared at 1e-10); the autotuner must keep results
+Every valid shape of every grid size (16 to 256) must give the default shape's effective
+coefficients (to the solver tolerance: rtol = 1e-11, compared at 1e-10), and the default
+shapes are checked against the oracle by the parity tests; the autotuner must keep results
 unchanged, record its choices in the cache file and reuse them."""
 import numpy as np
 import pytest
 
 import mch_inputs as mi
+from oracle import cell, plan
 from util import block_rel_err
 
 torch = pytest.importorskip("torch")
@@ -18,6 +20,10 @@ if not torch.cuda.is_available():
 import paper_2503_01276_gb300 as mch  # noqa: E402
 
 CASES = [("channel2d_17x17_L3", 128, 5, (4, 2, 1)), ("channel2d_17x17_L3", 32, 5, (2, 1))]
+SHAPE_CASES = [(name, n, m, st, "mixed") for (name, n, m, st) in CASES] + [
+    ("incl2d_33x33_L4", 256, 3, (1,), "mixed"),
+    ("channel2d_17x17_L3", 128, 5, (4, 2, 1), "fp64"),
+    ("channel2d_17x17_L3", 32, 5, (2, 1), "fp64")]
 
 
 def _media(wl, s):
@@ -38,12 +44,19 @@ def _solve(s, med, shapes=None):
     return Es
 
 
-@pytest.mark.parametrize("name,n_fine,macro,strides", CASES)
-def test_every_shape_matches_default(name, n_fine, macro, strides):
-    wl = mi.small_workload(name, n_fine=n_fine, macro_n=macro, strides=strides)
+@pytest.mark.parametrize("name,n_fine,macro,strides,precision", SHAPE_CASES)
+def test_every_shape_matches_default(name, n_fine, macro, strides, precision):
+    wl = mi.small_workload(name, n_fine=n_fine, macro_n=macro, strides=strides,
+                           precision=precision)
     s = mch.Solver.from_workload(wl, rtol=1e-11)
     med = _media(wl, s)
     ref = _solve(s, med)
+    # the default shape against the oracle, so that every shape is tied to it
+    pl = plan.level_plan(wl)
+    oref = cell.run_hierarchy(wl, pl, [mi.media(wl, l["points"], wl.n_level(k + 1))
+                                       for k, l in enumerate(pl)], keep_phi=False)
+    for lev in range(wl.n_levels):
+        assert block_rel_err(ref[lev], oref[lev]["E"], wl.n_cont, wl.dim) < 1e-9, lev
     counts = [s.variant(lev)[1] for lev in range(1, wl.n_levels + 1)]
     tried = 0
     for v in range(1, max(counts)):
@@ -61,6 +74,8 @@ def test_every_shape_matches_default(name, n_fine, macro, strides):
         for lev in range(wl.n_levels):
             err = block_rel_err(Es[lev], ref[lev], wl.n_cont, wl.dim)
             assert err < 1e-10, (v, lev + 1, shapes, err)
+            err = block_rel_err(Es[lev], oref[lev]["E"], wl.n_cont, wl.dim)
+            assert err < 1e-9, (v, lev + 1, shapes, err)
     assert tried > 0
 
 
