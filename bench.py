@@ -92,7 +92,14 @@ BYTES3D_PER_NODE_ITER_UNIT, BYTES3D_PER_NODE_ITER_POINT = 40, 14
 # DRAM bytes (read + write) per k_level2d launch from one ncu capture
 # (dram__bytes_read.sum + dram__bytes_write.sum), per workload and level. Valid only for
 # the kernel sources they were taken on: null is reported when the sources' hash differs.
-LEVEL_TRAFFIC = {}
+LEVEL_TRAFFIC = {
+    # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+    #     --clock-control none -k regex:k_level2d -s 12 -c 4 python bench.py --no-configs
+    #     --no-cpu --no-plain --steps 1 --warmup 3 --tiles 4,7,9,5   (the timed step's launches)
+    "incl2d_33x33_L4": {"sha256_16": "5e14af1f3715f415", "tiles": (4, 7, 9, 5),
+                        "bytes_per_launch": (101.346816e6, 117.472512e6, 111.101184e6,
+                                             134.148096e6)},
+}
 
 
 class ClockSampler:
@@ -146,7 +153,8 @@ class ClockSampler:
 def _sources_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("k_level.cuh", "k_level_f32.cu", "k_level_f32_alt.cu"):
+    for f in ("k_level.cuh", "k_level_f32.cu", "k_level_f32_alt.cu", "k_level_f32_alt2.cu",
+              "k_level_shapes.h"):
         with open(os.path.join(ROOT, "paper_2503_01276_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
