@@ -272,3 +272,32 @@ def test_coarse_blocks_odd_P_hierarchy(precision):
     for lev in range(wl.n_levels):
         err = block_rel_err(Eg[lev], Eo[lev]["E"], wl.n_cont, wl.dim)
         assert err < 1e-9, (lev + 1, err)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_inputs_are_read_only(precision):
+    """The library reads the caller's media and loss weights and never writes them: after a
+    forward pass over every level and a backward pass, the device buffers are bit-identical
+    to the host originals."""
+    wl = mi.small_workload("channel2d_17x17_L3", n_fine=128, macro_n=5, strides=(4, 2, 1),
+                           precision=precision)
+    s = mch.Solver.from_workload(wl, rtol=1e-11)
+    host, dev = [], []
+    for lev in range(1, wl.n_levels + 1):
+        k, l = mi.media(wl, s.level_points(lev), s.n_elem(lev))
+        host.append((k, l))
+        dev.append((torch.from_numpy(k).cuda(), torch.from_numpy(l).cuda()))
+        s.solve_level(lev, *dev[-1])
+    rng = np.random.default_rng(3)
+    W = [rng.standard_normal((s.num_points(l), s.R, s.R)) for l in range(1, wl.n_levels + 1)]
+    Wd = [torch.from_numpy(w).cuda() for w in W]
+    G = [torch.zeros((s.num_points(l), s.n_elem(l) ** 2), dtype=torch.float64, device="cuda")
+         for l in range(1, wl.n_levels + 1)]
+    s.backward(Wd, G)
+    torch.cuda.synchronize()
+    for (k, l), (kd, ld) in zip(host, dev):
+        assert np.array_equal(kd.cpu().numpy(), k)
+        assert np.array_equal(ld.cpu().numpy(), l)
+    for w, wd in zip(W, Wd):
+        assert np.array_equal(wd.cpu().numpy(), w)
+    s.close()
