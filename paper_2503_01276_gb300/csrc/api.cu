@@ -728,7 +728,7 @@ mch_status solve_range(mch_handle *h, int level, int p0, int p1, const double *k
                            L.Sinv64 + p0 * nc * nc, L.minv + p0 * L.nv, g + p0 * nc * R, bb,
                            L.x + u0 * L.nv, L.iters + u0, L.sweeps + u0, L.ratio + u0,
                            L.ustat + u0, (float)d.inner_tol, max_iter, d.rtol, d.max_refine, lam,
-                           bvec ? h->bnorm + u0 : nullptr, L0.variant};
+                           bvec ? h->bnorm + u0 : nullptr, L0.variant, h->yc + u0 * L.nv};
       CK(launch_level2d<double>(la, st), "level fp64");
     } else {
       LevelArgs<float> la{cn, R, L.n, P, N, nc, L.nv, ilog2(L.n / P), ilog2(P),
@@ -736,7 +736,7 @@ mch_status solve_range(mch_handle *h, int level, int p0, int p1, const double *k
                           L.Sinv64 + p0 * nc * nc, L.minv + p0 * L.nv, g + p0 * nc * R, bb,
                           L.x + u0 * L.nv, L.iters + u0, L.sweeps + u0, L.ratio + u0,
                           L.ustat + u0, (float)d.inner_tol, max_iter, d.rtol, d.max_refine, lam,
-                          bvec ? h->bnorm + u0 : nullptr, L0.variant};
+                          bvec ? h->bnorm + u0 : nullptr, L0.variant, h->yc + u0 * L.nv};
       CK(launch_level2d<float>(la, st), "level fp32");
     }
     ++h->launches;

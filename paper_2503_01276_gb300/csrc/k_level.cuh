@@ -89,6 +89,35 @@ __device__ __forceinline__ void add_lab(V (&acc)[NC], int lab, V v) {
 
 // Adds a node value to the per-label west/east slots of its four adjacent elements; the
 // north elements of an aligned strip's last row (to_next) go to `bins` directly.
+// Per-label sums of one element column of a strip: a running sum for the current label that
+// goes to the label's slot when the label changes (labels change rarely along a strip), so a
+// value costs one add instead of NC predicated adds. Used for the FP64 constraint sums of the
+// refinement steps, whose FP64 adds run at a small fraction of the FP32 rate.
+template <int NC, typename V>
+struct LabRun {
+  V acc[NC];
+  V cur;
+  int lab;
+  __device__ __forceinline__ void init(int l) {
+#pragma unroll
+    for (int j = 0; j < NC; ++j) acc[j] = V(0);
+    cur = V(0);
+    lab = l;
+  }
+  __device__ __forceinline__ void add(int l, V v) {
+    if (l != lab) {
+      add_lab<NC>(acc, lab, cur);
+      cur = V(0);
+      lab = l;
+    }
+    cur += v;
+  }
+  __device__ __forceinline__ void close() {
+    add_lab<NC>(acc, lab, cur);
+    cur = V(0);
+  }
+};
+
 // East slots to the owner lane of column c+1 (lane 31 adds its own directly), then sums over
 // the lanes that share the west sub-block; the group leader adds to `bins`.
 template <int NC, typename V>
@@ -183,6 +212,9 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
   const double *bvec = a.b ? a.b + (size_t)unit * a.nv : nullptr;
   const double *gt = a.g + (size_t)pt * nc * a.R + rfun;  // stride R
   double *xg = a.x + (size_t)unit * a.nv;
+  // FP64 residual of step (d) kept for step (e) when it does not fit in shared memory (else
+  // the FP64 stencil runs twice per refinement step)
+  double *r64g = (!SR && a.r64) ? a.r64 + (size_t)unit * a.nv : nullptr;
   for (int t = rank * THREADS + tid; t < a.nv; t += CL * THREADS) xg[t] = 0.0;
   for (int t = tid; t < (1 + NYB) * YB; t += THREADS) ps[t] = T(0);
   for (int t = tid; t < (ROWS + 1) * NEL; t += THREADS) {
@@ -339,10 +371,10 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
     // ================= FP64 refinement step =================
     // (a) fold the correction; (b) Ct x by element rows (column sums of node pairs)
     {
-      double aW[NC], aE[NC];
-#pragma unroll
-      for (int j = 0; j < NC; ++j) aW[j] = aE[j] = 0.0;
       int lS0 = lb[0], lS1 = lb[dEc];
+      LabRun<NC, double> rW, rE;
+      rW.init(lS0);
+      rE.init(lS1);
       double vprev = 0.0;
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
@@ -354,20 +386,22 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
         }
         x[i] = T(0);
         const double u = v + vprev;
-        add_lab<NC>(aW, lS0, u);
-        add_lab<NC>(aE, lS1, u);
+        rW.add(lS0, u);
+        rE.add(lS1, u);
         vprev = v;
         lS0 = lN0;
         lS1 = lN1;
       }
       if (!next_row) {
-        add_lab<NC>(aW, lS0, vprev);
-        add_lab<NC>(aE, lS1, vprev);
+        rW.add(lS0, vprev);
+        rE.add(lS1, vprev);
       } else if (nact == RPT) {
         atomicAdd(&red64[lS0 * nq + baseWn], vprev);
         atomicAdd(&red64[lS1 * nq + baseEn], vprev);
       }
-      flush_bins<NC>(aW, aE, red64, lane, seg, nq, baseW, baseE);
+      rW.close();
+      rE.close();
+      flush_bins<NC>(rW.acc, rE.acc, red64, lane, seg, nq, baseW, baseE);
     }
     C::sync();
     // mu = S^-1 (g - Ct x)
@@ -398,9 +432,6 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
     // (d) Ct M^-1 r with r = b - A x (FP64); r kept in shared memory when SR, else formed
     // again in (e)
     {
-      double aW[NC], aE[NC];
-#pragma unroll
-      for (int j = 0; j < NC; ++j) aW[j] = aE[j] = 0.0;
       // strips wholly beyond the last node row (nact = 0) read nothing from global memory
       const bool any = nact > 0;
       double xW0 = any ? xb[-XW - 1] : 0.0, xC0 = any ? xb[-XW] : 0.0;
@@ -408,6 +439,9 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
       double xC1 = any ? xb[0] : 0.0, xE1 = any ? xb[dEx] : 0.0;
       double kS0 = any ? kg[0] : 0.0, kS1 = any ? kg[dEc] : 0.0;
       int lS0 = lb[0], lS1 = lb[dEc];
+      LabRun<NC, double> rW, rE;
+      rW.init(lS0);
+      rE.init(lS1);
       double zprev = 0.0;
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
@@ -425,24 +459,27 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
           const double ax = q1_apply(kS0, kS1, kN0, kN1, xW0, xC0, xE0, xW1, xC1, xE1, xW2, xC2, xE2);
           const double rv = (bg ? bg[i * XW] : 0.0) - ax;
           if constexpr (SR) rs[(g * RPT + i) * W + kx] = rv;
+          else if (r64g) r64g[kx + XW * (ky0 + i)] = rv;
           zm = mg[i * XW] * rv;
         }
         const double u = zm + zprev;
-        add_lab<NC>(aW, lS0, u);
-        add_lab<NC>(aE, lS1, u);
+        rW.add(lS0, u);
+        rE.add(lS1, u);
         zprev = zm;
         xW0 = xW1; xC0 = xC1; xE0 = xE1;
         xW1 = xW2; xC1 = xC2; xE1 = xE2;
         kS0 = kN0; kS1 = kN1; lS0 = lN0; lS1 = lN1;
       }
       if (!next_row) {
-        add_lab<NC>(aW, lS0, zprev);
-        add_lab<NC>(aE, lS1, zprev);
+        rW.add(lS0, zprev);
+        rE.add(lS1, zprev);
       } else if (nact == RPT) {
         atomicAdd(&red64[nc + lS0 * nq + baseWn], zprev);
         atomicAdd(&red64[nc + lS1 * nq + baseEn], zprev);
       }
-      flush_bins<NC>(aW, aE, red64 + nc, lane, seg, nq, baseW, baseE);
+      rW.close();
+      rE.close();
+      flush_bins<NC>(rW.acc, rE.acc, red64 + nc, lane, seg, nq, baseW, baseE);
     }
     C::sync();
     if (warp == 0) {
@@ -460,7 +497,7 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
       double rho_p = 0.0;
       double xW0 = 0, xC0 = 0, xE0 = 0, xW1 = 0, xC1 = 0, xE1 = 0, kS0 = 0, kS1 = 0;
       if constexpr (!SR) {
-        if (nact > 0) {
+        if (nact > 0 && !r64g) {
           xW0 = xb[-XW - 1]; xC0 = xb[-XW]; xE0 = xb[-XW + dEx];
           xW1 = xb[-1]; xC1 = xb[0]; xE1 = xb[dEx];
           kS0 = kg[0]; kS1 = kg[dEc];
@@ -476,6 +513,8 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
         double rv = 0.0;
         if constexpr (SR) {
           if (act) rv = rs[(g * RPT + i) * W + kx];
+        } else if (r64g) {
+          if (act) rv = r64g[kx + XW * (ky0 + i)];
         } else {
           double xW2 = 0.0, xC2 = 0.0, xE2 = 0.0;
           if (act) {

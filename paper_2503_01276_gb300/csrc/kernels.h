@@ -50,6 +50,9 @@ struct LevelArgs {
   double *lam;            // [pt*R][nc] final multipliers (b - A x = Ct^T lam), or null
   const double *bnorm;    // [pt*R] b'M^-1 b (reference floor of the stopping test), or null
   int variant;            // launch shape (0 = default; see level2d_variant_ok)
+  double *r64;            // [pt*R][nv] scratch for the FP64 residual of shapes that cannot
+                          // keep it in shared memory (else it is formed twice per step), or
+                          // null
 };
 template <typename T>
 cudaError_t launch_level2d(const LevelArgs<T> &a, cudaStream_t st);
