@@ -776,9 +776,14 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
           push_halo(ps);
         }
         C::sync();  // B1: p and its halo visible; r1 cleared
-        // ---- q = A p; p.q and Ct M^-1 q
+        // ---- q = A p; p.q and Ct M^-1 q, accumulated in the same pass over the rows (no
+        // per-row arrays of M^-1 q and p are kept)
         {
-          T mq[RPT], pv[RPT];
+          T aW[NC], aE[NC];
+#pragma unroll
+          for (int j = 0; j < NC; ++j) aW[j] = aE[j] = T(0);
+          T pq = T(0), mqprev = T(0);
+          int lS0 = lb[0], lS1 = lb[dEc];
           T pW0 = pb[-W - 1], pC0 = pb[-W], pE0 = pb[-W + dEx];
           T pW1 = pb[-1], pC1 = pb[0], pE1 = pb[dEx];
           T kS0 = kb[0], kS1 = kb[dEc];
@@ -786,16 +791,31 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
           for (int i = 0; i < RPT; ++i) {
             const T pW2 = pb[(i + 1) * W - 1], pC2 = pb[(i + 1) * W], pE2 = pb[(i + 1) * W + dEx];
             const T kN0 = kb[(i + 1) * NEL], kN1 = kb[(i + 1) * NEL + dEc];
+            const int lN0 = lb[(i + 1) * NEL], lN1 = lb[(i + 1) * NEL + dEc];
             T qv = q1_apply(kS0, kS1, kN0, kN1, pW0, pC0, pE0, pW1, pC1, pE1, pW2, pC2, pE2);
             qv = i < nact ? qv : T(0);
             q[i] = qv;
-            mq[i] = mb[i * W] * qv;
-            pv[i] = pC1;
+            const T mq = mb[i * W] * qv;
+            pq += pC1 * qv;
+            const T u = mq + mqprev;
+            add_lab<NC>(aW, lS0, u);
+            add_lab<NC>(aE, lS1, u);
+            mqprev = mq;
             pW0 = pW1; pC0 = pC1; pE0 = pE1;
             pW1 = pW2; pC1 = pC2; pE1 = pE2;
             kS0 = kN0; kS1 = kN1;
+            lS0 = lN0; lS1 = lN1;
           }
-          ct_reduce(mq, pv, q, r1 + 1, r1);
+          if (!next_row) {
+            add_lab<NC>(aW, lS0, mqprev);
+            add_lab<NC>(aE, lS1, mqprev);
+          } else if (nact == RPT) {
+            atomicAdd(&r1[1 + lS0 * nq + baseWn], mqprev);
+            atomicAdd(&r1[1 + lS1 * nq + baseEn], mqprev);
+          }
+          flush_bins<NC>(aW, aE, r1 + 1, lane, seg, nq, baseW, baseE);
+          pq = warp_sum(pq);
+          if (lane == 0) atomicAdd(&r1[0], pq);
         }
         // every CTA read r2 (after B3) before B1, so it can be cleared for the next use
         for (int t = tid; t < NRED; t += THREADS) r2[t] = T(0);
