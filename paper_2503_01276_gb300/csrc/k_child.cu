@@ -220,59 +220,89 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram2d(int nv, int slices, const
   }
 }
 
+// b = scale * P^T y on the level grid (zero on its boundary nodes): P^T sums the fine values
+// around coarse node K with the separable hat weights (RHO - |d|) / RHO per axis. One CTA per
+// (unit, KB coarse rows): the fine rows those coarse rows reach are staged in shared memory
+// with coalesced loads, then summed along y per fine column and along x per coarse node.
 template <int RHO, class S>
-__global__ void k_restrict2d(int nf, const double *yf, int nvf, double scale, double *outc,
-                             int nvc) {
+__global__ void __launch_bounds__(256) k_restrict2d(int nf, const double *yf, int nvf,
+                                                     double scale, double *outc, int nvc) {
   using V = typename S::V;
-  const int unit = blockIdx.y;
+  constexpr int KB = RHO >= 8 ? 1 : 8 / RHO;           // coarse rows per CTA
+  constexpr int NR = (KB - 1) * RHO + 2 * RHO - 1;     // staged fine rows
+  __shared__ V rows[NR * 257];
+  __shared__ V cs[257];
+  const int unit = blockIdx.y, tid = threadIdx.x;
   const int ncg = nf / RHO, Wc = ncg + 1, Wf = nf + 1;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k >= Wc * Wc) return;
-  const int Kx = k % Wc, Ky = k / Wc;
-  double *o = outc + (size_t)unit * nvc;
-  if (Kx == 0 || Ky == 0 || Kx == ncg || Ky == ncg) {
-    o[k] = 0.0;
-    return;
-  }
-  const int c0 = (Ky * RHO) * Wf + Kx * RHO;
+  const int K0 = blockIdx.x * KB;
+  const int fr0 = K0 * RHO - (RHO - 1);                // first staged fine row (may be < 0)
   const typename S::P yb = S::vec(yf, unit, nvf);
-  V s = S::zero();
-#pragma unroll
-  for (int dy = -(RHO - 1); dy <= RHO - 1; ++dy) {
-    V sx = S::zero();
-#pragma unroll
-    for (int dx = -(RHO - 1); dx <= RHO - 1; ++dx)
-      sx += S::ldv(yb, nvf, c0 + dy * Wf + dx) * float(RHO - (dx < 0 ? -dx : dx));
-    s += sx * float(RHO - (dy < 0 ? -dy : dy));
+  for (int t = tid; t < NR * Wf; t += 256) {
+    const int fr = fr0 + t / Wf;
+    rows[t] = (fr >= 0 && fr <= nf) ? S::ldv(yb, nvf, fr * Wf + t % Wf) : S::zero();
   }
-  o[k] = scale * S::to(s) * (1.0 / (RHO * RHO));
+  __syncthreads();
+  double *o = outc + (size_t)unit * nvc;
+  for (int kk = 0; kk < KB; ++kk) {
+    const int Ky = K0 + kk;
+    if (Ky > ncg) break;                               // uniform over the CTA
+    if (Ky == 0 || Ky == ncg) {
+      for (int t = tid; t < Wc; t += 256) o[Ky * Wc + t] = 0.0;
+      continue;
+    }
+    for (int col = tid; col < Wf; col += 256) {
+      const V *rc = rows + (kk * RHO) * Wf + col;      // fine row Ky RHO - (RHO - 1)
+      V sy = S::zero();
+#pragma unroll
+      for (int d = 0; d < 2 * RHO - 1; ++d)
+        sy += rc[d * Wf] * float(RHO - (d < RHO - 1 ? RHO - 1 - d : d - (RHO - 1)));
+      cs[col] = sy;
+    }
+    __syncthreads();
+    for (int Kx = tid; Kx < Wc; Kx += 256) {
+      double v = 0.0;
+      if (Kx > 0 && Kx < ncg) {
+        const V *cc = cs + Kx * RHO - (RHO - 1);
+        V sx = S::zero();
+#pragma unroll
+        for (int d = 0; d < 2 * RHO - 1; ++d)
+          sx += cc[d] * float(RHO - (d < RHO - 1 ? RHO - 1 - d : d - (RHO - 1)));
+        v = scale * S::to(sx) * (1.0 / (RHO * RHO));
+      }
+      o[Ky * Wc + Kx] = v;
+    }
+    __syncthreads();                                   // cs is rewritten for the next row
+  }
 }
 
-// One thread per coarse cell: the cell's RHO x RHO fine nodes (lower-left corner included)
-// get the bilinear interpolant of the cell's four coarse values.
+// phi += P x: every fine node of the cells' lower-left quadrants (rows and columns 0 .. nf-1)
+// gets the bilinear interpolant of its coarse cell's four values. One CTA per (unit, KB
+// coarse rows = 8 fine rows), one thread per fine node (coalesced); the coarse values of the
+// CTA's KB + 1 coarse rows are converted once into shared memory.
 template <int RHO, class S>
-__global__ void k_prolong_add2d(int nf, const double *xc, int nvc, double *phif, int nvf) {
+__global__ void __launch_bounds__(256) k_prolong_add2d(int nf, const double *xc, int nvc,
+                                                        double *phif, int nvf) {
   using V = typename S::V;
-  const int unit = blockIdx.y;
+  constexpr int KB = RHO >= 8 ? 1 : 8 / RHO;
+  __shared__ V xs[(KB + 1) * 129];
+  const int unit = blockIdx.y, tid = threadIdx.x;
   const int ncg = nf / RHO, Wc = ncg + 1, Wf = nf + 1;
-  const int cell = blockIdx.x * blockDim.x + threadIdx.x;
-  if (cell >= ncg * ncg) return;
-  const int Kx = cell % ncg, Ky = cell / ncg;
-  const double *x = xc + (size_t)unit * nvc + Kx + Wc * Ky;
-  const V x00 = S::from(x[0]), x10 = S::from(x[1]), x01 = S::from(x[Wc]), x11 = S::from(x[Wc + 1]);
-  const int f0 = (Ky * RHO) * Wf + Kx * RHO;
+  const int K0 = blockIdx.x * KB;
+  const int kb = min(KB, ncg - K0);                    // coarse cell rows of this CTA
+  const double *x = xc + (size_t)unit * nvc + (size_t)K0 * Wc;
+  for (int t = tid; t < (kb + 1) * Wc; t += 256) xs[t] = S::from(x[t]);
+  __syncthreads();
   const typename S::P pf = S::vec(phif, unit, nvf);
-  const V dl = x01 - x00, dr = x11 - x10;
-#pragma unroll
-  for (int j = 0; j < RHO; ++j) {
-    const float ty = float(j) * (1.0f / RHO);  // exact: RHO is a power of two
-    const V aj = x00 + dl * ty, bj = x10 + dr * ty;
-    const V dj = bj - aj;
-#pragma unroll
-    for (int i = 0; i < RHO; ++i) {
-      const int k = f0 + j * Wf + i;
-      S::stv(pf, nvf, k, S::ldv(pf, nvf, k) + (aj + dj * (float(i) * (1.0f / RHO))));
-    }
+  for (int t = tid; t < kb * RHO * nf; t += 256) {
+    const int jr = t / nf, col = t - jr * nf;          // fine row K0 RHO + jr, column col
+    const int kr = jr / RHO, j = jr % RHO;
+    const int Kx = col / RHO, i = col % RHO;
+    const V *xr = xs + kr * Wc + Kx;
+    const V x00 = xr[0], x10 = xr[1], x01 = xr[Wc], x11 = xr[Wc + 1];
+    const float ty = float(j) * (1.0f / RHO);          // exact: RHO is a power of two
+    const V aj = x00 + (x01 - x00) * ty, bj = x10 + (x11 - x10) * ty;
+    const int k = (K0 * RHO + jr) * Wf + col;
+    S::stv(pf, nvf, k, S::ldv(pf, nvf, k) + (aj + (bj - aj) * (float(i) * (1.0f / RHO))));
   }
 }
 
@@ -339,8 +369,9 @@ cudaError_t launch_gram(int npts, int R, int nv, const double *X, const double *
 template <class S>
 cudaError_t restrict_s(int npts, int R, int nf, int rho, const double *yf, int nvf, double scale,
                        double *outc, int nvc, cudaStream_t st) {
-  const int Wc = nf / rho + 1;
-  dim3 grid((Wc * Wc + 255) / 256, npts * R);
+  if (nf > 256) return cudaErrorInvalidValue;
+  const int Wc = nf / rho + 1, kb = rho >= 8 ? 1 : 8 / rho;
+  dim3 grid((Wc + kb - 1) / kb, npts * R);
   switch (rho) {
     case 2: k_restrict2d<2, S><<<grid, 256, 0, st>>>(nf, yf, nvf, scale, outc, nvc); break;
     case 4: k_restrict2d<4, S><<<grid, 256, 0, st>>>(nf, yf, nvf, scale, outc, nvc); break;
@@ -359,12 +390,13 @@ cudaError_t launch_restrict2d(int npts, int R, int nf, int rho, const double *yf
 template <class S>
 cudaError_t prolong_s(int npts, int R, int nf, int rho, const double *xc, int nvc, double *phif,
                       int nvf, cudaStream_t st) {
-  const int ncg = nf / rho;
-  dim3 grid((ncg * ncg + 127) / 128, npts * R);
+  if (nf > 256) return cudaErrorInvalidValue;
+  const int ncg = nf / rho, kb = rho >= 8 ? 1 : 8 / rho;
+  dim3 grid((ncg + kb - 1) / kb, npts * R);
   switch (rho) {
-    case 2: k_prolong_add2d<2, S><<<grid, 128, 0, st>>>(nf, xc, nvc, phif, nvf); break;
-    case 4: k_prolong_add2d<4, S><<<grid, 128, 0, st>>>(nf, xc, nvc, phif, nvf); break;
-    case 8: k_prolong_add2d<8, S><<<grid, 128, 0, st>>>(nf, xc, nvc, phif, nvf); break;
+    case 2: k_prolong_add2d<2, S><<<grid, 256, 0, st>>>(nf, xc, nvc, phif, nvf); break;
+    case 4: k_prolong_add2d<4, S><<<grid, 256, 0, st>>>(nf, xc, nvc, phif, nvf); break;
+    case 8: k_prolong_add2d<8, S><<<grid, 256, 0, st>>>(nf, xc, nvc, phif, nvf); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

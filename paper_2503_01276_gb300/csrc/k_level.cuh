@@ -133,6 +133,24 @@ __device__ __forceinline__ void flush_bins(V (&aW)[NC], V (&aE)[NC], V *bins, in
   }
 }
 
+// The north element row of a strip that ends a sub-block row (pred: next_row with every row
+// of the strip active) lies in the next sub-block row: its per-label west/east values go
+// through the same warp reduction as the strip's own sums, so that one atomic per segment,
+// not one per thread, reaches a bin. Lanes without the predicate add zero; the call is skipped
+// by warps where no lane has it.
+template <int NC, typename V>
+__device__ __forceinline__ void flush_next(bool pred, int lW, int lE, V v, V *bins, int lane,
+                                           int seg, int nq, int baseWn, int baseEn) {
+  if (!__any_sync(0xffffffffu, pred)) return;
+  V nW[NC], nE[NC];
+#pragma unroll
+  for (int j = 0; j < NC; ++j) nW[j] = nE[j] = V(0);
+  const V u = pred ? v : V(0);
+  add_lab<NC>(nW, lW, u);
+  add_lab<NC>(nE, lE, u);
+  flush_bins<NC>(nW, nE, bins, lane, seg, nq, baseWn, baseEn);
+}
+
 // Chebyshev coefficients of the preconditioner on [1/50, 2]: y_1 = c0 M^-1 r and, for step
 // j = 1 .. NCH-1, d_j = c1[j] d_{j-1} + c2[j] M^-1 (r - A y_j), y_{j+1} = y_j + d_j.
 struct ChebCoef {
@@ -354,10 +372,9 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
     if (!next_row) {
       add_lab<NC>(aW, lS0, vprev);
       add_lab<NC>(aE, lS1, vprev);
-    } else if (nact == RPT) {
-      atomicAdd(&bins[lS0 * nq + baseWn], vprev);
-      atomicAdd(&bins[lS1 * nq + baseEn], vprev);
     }
+    flush_next<NC>(next_row && nact == RPT, lS0, lS1, vprev, bins, lane, seg, nq,
+                   baseWn, baseEn);
     flush_bins<NC>(aW, aE, bins, lane, seg, nq, baseW, baseE);
     dsum = warp_sum(dsum);
     if (lane == 0) atomicAdd(dot, dsum);
@@ -395,10 +412,9 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
       if (!next_row) {
         rW.add(lS0, vprev);
         rE.add(lS1, vprev);
-      } else if (nact == RPT) {
-        atomicAdd(&red64[lS0 * nq + baseWn], vprev);
-        atomicAdd(&red64[lS1 * nq + baseEn], vprev);
       }
+      flush_next<NC>(next_row && nact == RPT, lS0, lS1, vprev, red64, lane, seg, nq,
+                     baseWn, baseEn);
       rW.close();
       rE.close();
       flush_bins<NC>(rW.acc, rE.acc, red64, lane, seg, nq, baseW, baseE);
@@ -473,10 +489,9 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
       if (!next_row) {
         rW.add(lS0, zprev);
         rE.add(lS1, zprev);
-      } else if (nact == RPT) {
-        atomicAdd(&red64[nc + lS0 * nq + baseWn], zprev);
-        atomicAdd(&red64[nc + lS1 * nq + baseEn], zprev);
       }
+      flush_next<NC>(next_row && nact == RPT, lS0, lS1, zprev, red64 + nc, lane, seg, nq,
+                     baseWn, baseEn);
       rW.close();
       rE.close();
       flush_bins<NC>(rW.acc, rE.acc, red64 + nc, lane, seg, nq, baseW, baseE);
@@ -630,12 +645,11 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
             add_lab<NC>(azE, lS1, zprev);
             add_lab<NC>(aqW, lS0, mqprev);
             add_lab<NC>(aqE, lS1, mqprev);
-          } else if (nact == RPT) {
-            atomicAdd(&rb[4 + lS0 * nq + baseWn], zprev);
-            atomicAdd(&rb[4 + lS1 * nq + baseEn], zprev);
-            atomicAdd(&rb[4 + nc + lS0 * nq + baseWn], mqprev);
-            atomicAdd(&rb[4 + nc + lS1 * nq + baseEn], mqprev);
           }
+          flush_next<NC>(next_row && nact == RPT, lS0, lS1, zprev, rb + 4, lane, seg, nq, baseWn,
+                         baseEn);
+          flush_next<NC>(next_row && nact == RPT, lS0, lS1, mqprev, rb + 4 + nc, lane, seg, nq,
+                         baseWn, baseEn);
           flush_bins<NC>(azW, azE, rb + 4, lane, seg, nq, baseW, baseE);
           flush_bins<NC>(aqW, aqE, rb + 4 + nc, lane, seg, nq, baseW, baseE);
           pq = warp_sum(pq);
@@ -809,10 +823,9 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
           if (!next_row) {
             add_lab<NC>(aW, lS0, mqprev);
             add_lab<NC>(aE, lS1, mqprev);
-          } else if (nact == RPT) {
-            atomicAdd(&r1[1 + lS0 * nq + baseWn], mqprev);
-            atomicAdd(&r1[1 + lS1 * nq + baseEn], mqprev);
           }
+          flush_next<NC>(next_row && nact == RPT, lS0, lS1, mqprev, r1 + 1, lane, seg, nq,
+                         baseWn, baseEn);
           flush_bins<NC>(aW, aE, r1 + 1, lane, seg, nq, baseW, baseE);
           pq = warp_sum(pq);
           if (lane == 0) atomicAdd(&r1[0], pq);
