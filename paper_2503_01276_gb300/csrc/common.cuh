@@ -54,17 +54,12 @@ __device__ __forceinline__ void add_by_label(T (&acc)[MCH_MAX_CONT], int lab, T 
   for (int j = 0; j < MCH_MAX_CONT; ++j) acc[j] += (lab == j) ? v : T(0);
 }
 
-// 2D Q1 stencil at a node from the four adjacent kappas (a = SW, b = SE, c = NW, d = NE;
-// h^{d-2} = 1 in 2D) and the 3x3 neighbourhood of x. Element matrix entries 2/3 (same node),
-// -1/6 (edge neighbour), -1/3 (opposite corner).
-// The same stencil for any value type with +, - and products by float (FP64 or float-float);
-// sixth = 1/6 in that type.
-template <typename V>
-__device__ __forceinline__ V q1v(V a, V b, V c, V d, V xSW, V xS, V xSE, V xW, V x0, V xE, V xNW,
-                                 V xN, V xNE, V sixth) {
-  const V t = (a + b + c + d) * x0 * 4.0f - (b + d) * xE - (a + c) * xW - (c + d) * xN -
-              (a + b) * xS - (d * xNE + c * xNW + b * xSE + a * xSW) * 2.0f;
-  return t * sixth;
+// acc[lab] += v for a label held in a register (predicated adds into static slots; labels
+// >= NC add nothing)
+template <int NC, typename V>
+__device__ __forceinline__ void add_lab(V (&acc)[NC], int lab, V v) {
+#pragma unroll
+  for (int j = 0; j < NC; ++j) acc[j] += (lab == j) ? v : V(0);
 }
 
 template <typename T>

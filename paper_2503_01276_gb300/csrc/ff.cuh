@@ -80,6 +80,38 @@ __device__ __forceinline__ ff &operator-=(ff &a, ff b) { return a = a - b; }
 // acc += p
 __device__ __forceinline__ void ff_acc(ff &acc, ff p) { acc = acc + p; }
 
+// Exact scaling by a power of two.
+__device__ __forceinline__ ff ff_scale2(ff a, float pow2) { return ff{a.h * pow2, a.l * pow2}; }
+
+// Sum of products of double-words in the manner of Ogita, Rump and Oishi's Dot2 ("Accurate
+// sum and dot product", SIAM J. Sci. Comput. 26, 2005): the high words' products are split
+// exactly (two_prod) and summed with two_sum into s; every rounding error of those steps and
+// the cross terms a.h b.l + a.l b.h (themselves ~u of the product) go into one FP32 word e.
+// About 11 FP32 instructions per term instead of ~18 for a double-word product and sum, with
+// an error of the same kind (~n u^2 times the sum of the terms' magnitudes).
+struct ffdot {
+  float s, e;
+};
+__device__ __forceinline__ void dot_add(ffdot &d, ff a, ff b) {
+  const float p = __fmul_rn(a.h, b.h);
+  const float pe = __fmaf_rn(a.h, b.h, -p);
+  float s, t;
+  two_sum(d.s, p, s, t);
+  d.s = s;
+  d.e = __fadd_rn(d.e, __fadd_rn(t, __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, pe))));
+}
+__device__ __forceinline__ void dot_add(ffdot &d, ff a) {
+  float s, t;
+  two_sum(d.s, a.h, s, t);
+  d.s = s;
+  d.e = __fadd_rn(d.e, __fadd_rn(t, a.l));
+}
+__device__ __forceinline__ ff dot_get(ffdot d) {
+  float s, e;
+  two_sum(d.s, d.e, s, e);
+  return ff{s, e};
+}
+
 // plane access: vector v (index of a whole vector) of a batch with stride nv entries
 __device__ __forceinline__ ff ff_load(const double *base, size_t v, int nv, int k) {
   const float *p = reinterpret_cast<const float *>(base) + v * 2 * (size_t)nv;
@@ -106,8 +138,13 @@ struct F64S {
   __device__ static double to(V x) { return x; }
   __device__ static V zero() { return 0.0; }
   __device__ static V shfl_xor(V v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
-  // acc += x * y + y' * x'
-  __device__ static void acc2(V &acc, V x, V y, V x2, V y2) { acc += x * y + x2 * y2; }
+  // sums of products (Dot2 accumulator in float-float storage)
+  using D = double;
+  __device__ static D dzero() { return 0.0; }
+  __device__ static void dadd(D &d, V a, V b) { d += a * b; }
+  __device__ static void dadd(D &d, V a) { d += a; }
+  __device__ static V dget(D d) { return d; }
+  __device__ static V scale2(V a, float p2) { return a * (double)p2; }
 };
 
 struct FFS {
@@ -129,7 +166,12 @@ struct FFS {
   __device__ static V shfl_xor(V v, int o) {
     return ff{__shfl_xor_sync(0xffffffffu, v.h, o), __shfl_xor_sync(0xffffffffu, v.l, o)};
   }
-  __device__ static void acc2(V &acc, V x, V y, V x2, V y2) { ff_acc(acc, x * y + x2 * y2); }
+  using D = ffdot;
+  __device__ static D dzero() { return ffdot{0.f, 0.f}; }
+  __device__ static void dadd(D &d, V a, V b) { dot_add(d, a, b); }
+  __device__ static void dadd(D &d, V a) { dot_add(d, a); }
+  __device__ static V dget(D d) { return dot_get(d); }
+  __device__ static V scale2(V a, float p2) { return ff_scale2(a, p2); }
 };
 
 }  // namespace mch

@@ -34,8 +34,39 @@ __device__ __forceinline__ typename S::V seg_sum_s(typename S::V v, int seg) {
   return v;
 }
 
+template <int NC, class S>
+__device__ __forceinline__ void add_lab_s(typename S::V (&acc)[NC], int lab, typename S::V v) {
+#pragma unroll
+  for (int j = 0; j < NC; ++j) acc[j] += (lab == j) ? v : S::zero();
+}
+
 constexpr int CF_THREADS = 256;
 constexpr int CF_BR = 16;   // fine rows per band
+
+// A_1 x at a level-1 node: the Q1 stencil (element matrix entries 2/3 on the diagonal, -1/6
+// for an edge neighbour, -1/3 for the opposite corner; h^(d-2) = 1 in 2D) from the kappa of
+// the node's four elements (a SW, b SE, c NW, d NE) and the 3x3 values around it (tr points
+// at the node, rows W apart), as one sum of nine products: 4 (a+b+c+d) x0 - (b+d) xE - (a+c) xW - (c+d) xN - (a+b) xS
+// - 2 (d xNE + c xNW + b xSE + a xSW), times 1/6.
+template <class S>
+__device__ __forceinline__ typename S::V q1_dot(typename S::V a, typename S::V b,
+                                                typename S::V c, typename S::V d,
+                                                const typename S::V *tr, int W,
+                                                typename S::V sixth) {
+  using V = typename S::V;
+  const V ab = a + b, cd = c + d;
+  typename S::D t = S::dzero();
+  S::dadd(t, S::scale2(ab + cd, 4.f), tr[0]);
+  S::dadd(t, -(b + d), tr[1]);
+  S::dadd(t, -(a + c), tr[-1]);
+  S::dadd(t, -cd, tr[W]);
+  S::dadd(t, -ab, tr[-W]);
+  S::dadd(t, S::scale2(d, -2.f), tr[W + 1]);
+  S::dadd(t, S::scale2(c, -2.f), tr[W - 1]);
+  S::dadd(t, S::scale2(b, -2.f), tr[-W + 1]);
+  S::dadd(t, S::scale2(a, -2.f), tr[-W - 1]);
+  return S::dget(t) * sixth;
+}
 
 template <int NC, class S>
 __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
@@ -50,25 +81,43 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
   __shared__ double bins[MCH_MAX_NC];
   __shared__ typename S::P pp[4];
   __shared__ V pw[4];
+  __shared__ int nslot;
   const int tid = threadIdx.x;
-  if (tid < a.slots) {
-    pw[tid] = S::from(a.par_w[pt * a.slots + tid]);
-    const double *b = a.par_ptr[pt * a.slots + tid];
-    pp[tid] = b ? S::vec(b, r, a.nvf) : nullptr;
+  if (tid == 0) {
+    // the parents with a cell function, packed to the front
+    int ns = 0;
+    for (int s = 0; s < a.slots && s < 4; ++s) {
+      const double *b = a.par_ptr[pt * a.slots + s];
+      if (!b) continue;
+      pp[ns] = S::vec(b, r, a.nvf);
+      pw[ns] = S::from(a.par_w[pt * a.slots + s]);
+      ++ns;
+    }
+    nslot = ns;
   }
   for (int t = tid; t < a.nc; t += CF_THREADS) bins[t] = 0.0;
   __syncthreads();
 
-  // I on rows row_lo-1 .. row_lo+CF_BR (rows outside the lattice are zero)
-  for (int t = tid; t < (CF_BR + 2) * W; t += CF_THREADS) {
-    const int row = row_lo - 1 + t / W, col = t % W;
-    V v = S::zero();
-    if (row >= 0 && row <= nf) {
-      const int k = col + W * row;
-      for (int s = 0; s < a.slots; ++s)
-        if (pp[s]) v += pw[s] * S::ldv(pp[s], a.nvf, k);
+  // I on rows row_lo-1 .. row_lo+CF_BR (rows outside the lattice are zero); (row, col) of
+  // entry t advance without divisions
+  {
+    const int ns = nslot;
+    int row = row_lo - 1 + tid / W, col = tid % W;
+    for (int t = tid; t < (CF_BR + 2) * W; t += CF_THREADS) {
+      V v = S::zero();
+      if (row >= 0 && row <= nf) {
+        const int k = col + W * row;
+        typename S::D acc = S::dzero();
+        for (int s = 0; s < ns; ++s) S::dadd(acc, pw[s], S::ldv(pp[s], a.nvf, k));
+        v = S::dget(acc);
+      }
+      tile[t] = v;
+      col += CF_THREADS;
+      while (col >= W) {
+        col -= W;
+        ++row;
+      }
     }
-    tile[t] = v;
   }
   __syncthreads();
 
@@ -82,55 +131,65 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
     if constexpr (std::is_same<V, ff>::value) return ff_load(a.kappa_ff, pt, ncg * ncg, e);
     else return kc[e];
   };
-  for (int t = tid; t < (row_hi - row_lo) * W; t += CF_THREADS) {
-    const int row = row_lo + t / W, col = t % W;
-    const int k = col + W * row;
-    const V *tr = tile + (row - row_lo + 1) * W + col;
-    S::stv(phv, a.nvf, k, tr[0]);
-    V v = S::zero(), vR = S::zero();
-    if (row > 0 && row < nf && col > 0 && col < nf) {
-      const int e0x = (col - 1) >> lgr, e1x = col >> lgr;
-      const int e0y = (row - 1) >> lgr, e1y = row >> lgr;
-      const V kSW = kval(e0x + ncg * e0y), kSE = kval(e1x + ncg * e0y);
-      const V kNW = kval(e0x + ncg * e1y), kNE = kval(e1x + ncg * e1y);
-      v = q1v<V>(kSW, kSE, kNW, kNE, tr[-W - 1], tr[-W], tr[-W + 1], tr[-1], tr[0], tr[1],
-                 tr[W - 1], tr[W], tr[W + 1], sixth);
-      if (a.yR) {
-        // the same with kappa zero outside the integration region (period index of each
-        // adjacent fine element)
-        const int P = a.P, o = a.overs;
-        auto in = [&](int ex, int ey) {
-          const int px = ex >> a.lgmf, py = ey >> a.lgmf;
-          return px >= o && px < P - o && py >= o && py < P - o;
-        };
-        const V z = S::zero();
-        vR = q1v<V>(in(col - 1, row - 1) ? kSW : z, in(col, row - 1) ? kSE : z,
-                    in(col - 1, row) ? kNW : z, in(col, row) ? kNE : z, tr[-W - 1], tr[-W],
-                    tr[-W + 1], tr[-1], tr[0], tr[1], tr[W - 1], tr[W], tr[W + 1], sixth);
+  {
+    int row = row_lo + tid / W, col = tid % W;
+    for (int t = tid; t < (row_hi - row_lo) * W; t += CF_THREADS) {
+      const int k = col + W * row;
+      const V *tr = tile + (row - row_lo + 1) * W + col;
+      S::stv(phv, a.nvf, k, tr[0]);
+      V v = S::zero(), vR = S::zero();
+      if (row > 0 && row < nf && col > 0 && col < nf) {
+        const int e0x = (col - 1) >> lgr, e1x = col >> lgr;
+        const int e0y = (row - 1) >> lgr, e1y = row >> lgr;
+        const V kSW = kval(e0x + ncg * e0y), kSE = kval(e1x + ncg * e0y);
+        const V kNW = kval(e0x + ncg * e1y), kNE = kval(e1x + ncg * e1y);
+        v = q1_dot<S>(kSW, kSE, kNW, kNE, tr, W, sixth);
+        if (a.yR) {
+          // the same with kappa zero outside the integration region (period index of each
+          // adjacent fine element)
+          const int P = a.P, o = a.overs;
+          auto in = [&](int ex, int ey) {
+            const int px = ex >> a.lgmf, py = ey >> a.lgmf;
+            return px >= o && px < P - o && py >= o && py < P - o;
+          };
+          const V z = S::zero();
+          vR = q1_dot<S>(in(col - 1, row - 1) ? kSW : z, in(col, row - 1) ? kSE : z,
+                         in(col - 1, row) ? kNW : z, in(col, row) ? kNE : z, tr, W, sixth);
+        }
+      }
+      S::stv(yv, a.nvf, k, v);
+      if (yrv) S::stv(yrv, a.nvf, k, vR);
+      col += CF_THREADS;
+      while (col >= W) {
+        col -= W;
+        ++row;
       }
     }
-    S::stv(yv, a.nvf, k, v);
-    if (yrv) S::stv(yrv, a.nvf, k, vR);
   }
 
   // C_1 I on the band's element rows: element corner sums per (label, sub-block). Warp w
-  // takes column chunk w % nch (32 element columns: whole sub-block columns or aligned
-  // parts of one; lanes past the last column add nothing) and every rstep-th row, rstep =
-  // 8 / nch; warps beyond nch * rstep have no rows.
+  // takes column chunk w % nch (32 element columns: whole sub-block columns or aligned parts
+  // of one; lanes past the last column add nothing) and a contiguous range of the band's
+  // element rows (group w / nch). A lane walks its element column upwards with the sum of
+  // the node pair (ex, ex+1) of the previous node row, so an element costs two adds, and sums
+  // the elements of one level-n element (one label, one sub-block: the level-n element size
+  // 2^lgr divides the sub-block size) before adding them to its label's slot.
   {
     const int warp = tid >> 5, lane = tid & 31;
     const int nch = (nf + 31) >> 5;                // nf <= 256
-    const int chunk = warp % nch, rstep = (CF_THREADS / 32) / nch;
+    const int ngrp = (CF_THREADS / 32) / nch;
+    const int chunk = warp % nch, grp = warp / nch;
     const int ex = chunk * 32 + lane;
     const bool lane_ok = ex < nf;
+    const int exs = lane_ok ? ex : 0;
     const int lgm = a.lgmf, m = 1 << lgm;
     const int seg = m < 32 ? m : 32;
-    const uint8_t *lc = a.labels_c + (size_t)pt * ncg * ncg;
+    const int rho_m = (1 << lgr) - 1;
+    const uint8_t *lc = a.labels_c + (size_t)pt * ncg * ncg + (exs >> lgr);
+    const int bx = exs >> lgm;
     V acc[NC];
 #pragma unroll
     for (int j = 0; j < NC; ++j) acc[j] = S::zero();
-    const int erow_hi = min(row_lo + CF_BR, nf);
-    const int bx = ex >> lgm;
     auto flush = [&](int by) {
 #pragma unroll
       for (int j = 0; j < NC; ++j) {
@@ -140,25 +199,35 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
         acc[j] = S::zero();
       }
     };
-    // rows of one warp share ey, so the flush condition is uniform over the warp
-    int by_cur = -1;
-    const int ey0 = warp < nch * rstep ? row_lo + warp / nch : erow_hi;
-    for (int ey = ey0; ey < erow_hi; ey += rstep) {
-      const int by = ey >> lgm;
-      if (by != by_cur) {
-        if (by_cur >= 0) flush(by_cur);
-        by_cur = by;
+    const int erow_hi = min(row_lo + CF_BR, nf);
+    const int rpg = (CF_BR + ngrp - 1) / ngrp;
+    const int ey_lo = grp < ngrp ? min(row_lo + grp * rpg, erow_hi) : erow_hi;
+    const int ey_hi = min(ey_lo + rpg, erow_hi);
+    if (ey_lo < ey_hi) {                           // uniform over the warp
+      const V *tc = tile + (ey_lo - row_lo + 1) * W + exs;
+      V cprev = lane_ok ? tc[0] + tc[1] : S::zero();
+      V cur = S::zero();
+      int lab = lc[ncg * (ey_lo >> lgr)];
+      int by_cur = ey_lo >> lgm;
+      for (int ey = ey_lo; ey < ey_hi; ++ey) {
+        if (ey > ey_lo && (ey & rho_m) == 0) {     // a new level-n element row
+          add_lab_s<NC, S>(acc, lab, cur);
+          cur = S::zero();
+          const int by = ey >> lgm;
+          if (by != by_cur) {
+            flush(by_cur);
+            by_cur = by;
+          }
+          lab = lc[ncg * (ey >> lgr)];
+        }
+        tc += W;
+        const V cn = lane_ok ? tc[0] + tc[1] : S::zero();
+        cur += cprev + cn;
+        cprev = cn;
       }
-      if (lane_ok) {
-        const V *tr = tile + (ey - row_lo + 1) * W + ex;
-        const V sv = (tr[0] + tr[1]) + (tr[W] + tr[W + 1]);
-        const int l = lc[(ex >> lgr) + ncg * (ey >> lgr)];
-#pragma unroll
-        for (int j = 0; j < NC; ++j)
-          if (l == j) acc[j] += sv;
-      }
+      add_lab_s<NC, S>(acc, lab, cur);
+      flush(by_cur);
     }
-    if (by_cur >= 0) flush(by_cur);
   }
   __syncthreads();
   for (int t = tid; t < a.nc; t += CF_THREADS)
@@ -169,6 +238,7 @@ constexpr int GR_THREADS = 256;
 
 // E += alpha sym(X^T Y) per point (R vectors each). SYM: Y is the image of X under a
 // symmetric operator (Y = A_1 X), so X^T Y is symmetric and one product per pair suffices.
+// Each thread's pair sums are sums of products (S::D: Dot2 in float-float storage).
 template <int R, class S, bool SYM>
 __global__ void __launch_bounds__(GR_THREADS) k_gram2d(int nv, int slices, const double *X,
                                                         const double *Y, double alpha, double *E) {
@@ -177,9 +247,9 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram2d(int nv, int slices, const
   const int pt = blockIdx.x;
   const int per = (nv + slices - 1) / slices;
   const int k0 = blockIdx.y * per, k1 = min(nv, k0 + per);
-  V acc[NP];
+  typename S::D acc[NP];
 #pragma unroll
-  for (int p = 0; p < NP; ++p) acc[p] = S::zero();
+  for (int p = 0; p < NP; ++p) acc[p] = S::dzero();
   const typename S::P x0 = S::vec(X, (size_t)pt * R, nv), y0 = S::vec(Y, (size_t)pt * R, nv);
   // vector r of the point starts r * (entries of one vector) after vector 0
   const int vstride = (int)(S::vec(X, 1, nv) - S::vec(X, 0, nv));
@@ -195,15 +265,15 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram2d(int nv, int slices, const
     for (int r = 0; r < R; ++r)
 #pragma unroll
       for (int s = r; s < R; ++s, ++p) {
-        if constexpr (SYM) acc[p] = acc[p] + xv[r] * yv[s];
-        else S::acc2(acc[p], xv[r], yv[s], yv[r], xv[s]);
+        S::dadd(acc[p], xv[r], yv[s]);
+        if constexpr (!SYM) S::dadd(acc[p], yv[r], xv[s]);
       }
   }
   __shared__ double red[GR_THREADS / 32][NP];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
   for (int p = 0; p < NP; ++p) {
-    const V v = seg_sum_s<S>(acc[p], 32);
+    const V v = seg_sum_s<S>(S::dget(acc[p]), 32);
     if (lane == 0) red[w][p] = S::to(v);
   }
   __syncthreads();
@@ -237,9 +307,16 @@ __global__ void __launch_bounds__(256) k_restrict2d(int nf, const double *yf, in
   const int K0 = blockIdx.x * KB;
   const int fr0 = K0 * RHO - (RHO - 1);                // first staged fine row (may be < 0)
   const typename S::P yb = S::vec(yf, unit, nvf);
-  for (int t = tid; t < NR * Wf; t += 256) {
-    const int fr = fr0 + t / Wf;
-    rows[t] = (fr >= 0 && fr <= nf) ? S::ldv(yb, nvf, fr * Wf + t % Wf) : S::zero();
+  {
+    int fr = fr0 + tid / Wf, col = tid % Wf;          // advanced without divisions
+    for (int t = tid; t < NR * Wf; t += 256) {
+      rows[t] = (fr >= 0 && fr <= nf) ? S::ldv(yb, nvf, fr * Wf + col) : S::zero();
+      col += 256;
+      while (col >= Wf) {
+        col -= Wf;
+        ++fr;
+      }
+    }
   }
   __syncthreads();
   double *o = outc + (size_t)unit * nvc;
@@ -293,8 +370,8 @@ __global__ void __launch_bounds__(256) k_prolong_add2d(int nf, const double *xc,
   for (int t = tid; t < (kb + 1) * Wc; t += 256) xs[t] = S::from(x[t]);
   __syncthreads();
   const typename S::P pf = S::vec(phif, unit, nvf);
+  int jr = tid / nf, col = tid % nf;                  // fine row K0 RHO + jr, column col
   for (int t = tid; t < kb * RHO * nf; t += 256) {
-    const int jr = t / nf, col = t - jr * nf;          // fine row K0 RHO + jr, column col
     const int kr = jr / RHO, j = jr % RHO;
     const int Kx = col / RHO, i = col % RHO;
     const V *xr = xs + kr * Wc + Kx;
@@ -303,6 +380,11 @@ __global__ void __launch_bounds__(256) k_prolong_add2d(int nf, const double *xc,
     const V aj = x00 + (x01 - x00) * ty, bj = x10 + (x11 - x10) * ty;
     const int k = (K0 * RHO + jr) * Wf + col;
     S::stv(pf, nvf, k, S::ldv(pf, nvf, k) + (aj + (bj - aj) * (float(i) * (1.0f / RHO))));
+    col += 256;
+    while (col >= nf) {
+      col -= nf;
+      ++jr;
+    }
   }
 }
 

@@ -81,12 +81,6 @@ struct ClusterOps {
   }
 };
 
-template <int NC, typename V>
-__device__ __forceinline__ void add_lab(V (&acc)[NC], int lab, V v) {
-#pragma unroll
-  for (int j = 0; j < NC; ++j) acc[j] += (lab == j) ? v : V(0);
-}
-
 // Adds a node value to the per-label west/east slots of its four adjacent elements; the
 // north elements of an aligned strip's last row (to_next) go to `bins` directly.
 // Per-label sums of one element column of a strip: a running sum for the current label that
@@ -176,6 +170,7 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
   using C = ClusterOps<CL>;
   constexpr int THREADS = NEL * RG;
   constexpr int NWARPS = THREADS / 32;
+  static_assert(THREADS >= MCH_MAX_NC, "the small products give every row a thread");
   constexpr int ROWS = RG * RPT;
   constexpr int W = NEL + 1;
   constexpr int YB = (ROWS + 2) * W;                  // one halo-padded slab
@@ -201,9 +196,10 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
   T *ks = yb + NYB * YB;                              // [(ROWS+1)][NEL] kappa rows r_lo-1..
   T *sinv = ks + (ROWS + 1) * NEL;                    // [nc][nc] (symmetric)
   T *red = sinv + nc * nc;                            // [2][NRED] (two reduction buffers)
-  T *twarp = red + 2 * NRED;                          // [NWARPS][NRED]
-  T *lamw = twarp + NWARPS * NRED;                    // [NWARPS][nc]
-  T *mis = lamw + NWARPS * nc;                        // [ROWS][W] M^-1 of own rows
+  constexpr int NSC = NCH > 1 ? 1 : NWARPS;            // copies of the gathered sums
+  T *twarp = red + 2 * NRED;                          // [NSC][NRED]
+  T *lamw = twarp + NSC * NRED;                       // [NSC][nc]
+  T *mis = lamw + NSC * nc;                           // [ROWS][W] M^-1 of own rows
   T *chc = mis + ROWS * W;                            // [2][16] Chebyshev coefficients
   uint8_t *ls = reinterpret_cast<uint8_t *>(chc + 32);  // [(ROWS+1)][NEL]
 
@@ -287,8 +283,10 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
     const T dg = q1_diag(kb[i * NEL], kb[i * NEL + dEc], kb[(i + 1) * NEL], kb[(i + 1) * NEL + dEc]);
     mb[i * W] = (i < nact) ? T(1) / dg : T(0);   // each thread reads only its own entries
   }
-  T *tw = twarp + warp * NRED;
-  T *lw = lamw + warp * nc;
+  // gathered sums and multipliers: per warp in the Jacobi sweep (every warp evaluates them
+  // itself), shared by the CTA in the Chebyshev sweep (evaluated cooperatively)
+  T *tw = twarp + (NCH > 1 ? 0 : warp) * NRED;
+  T *lw = lamw + (NCH > 1 ? 0 : warp) * nc;
 
   // halo rows of a shared-memory slab (p or a Chebyshev iterate) to the neighbouring CTAs
   auto push_halo = [&](T *slab) {
@@ -297,20 +295,41 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
       if (g == RG - 1 && rank < CL - 1) C::remote(slab, rank + 1)[kx] = slab[ROWS * W + kx];
     }
   };
-  // small FP64 product out = S^-1 v by warp 0 (v, out in shared memory)
+  // Small products S^-1 v by the whole CTA: row i of S^-1 (symmetric) goes to KS consecutive
+  // threads (KS a power of two with KS nc <= THREADS, at most 32), each summing every KS-th
+  // term, then a KS-lane butterfly; so the work is spread over the CTA instead of repeated
+  // by every warp, and no row is a long serial chain.
+  const int KS = [&] {
+    int k = 1;
+    while (k < 32 && 2 * k * nc <= THREADS) k *= 2;
+    return k;
+  }();
+  const int srow = tid / KS, spart = tid % KS;
+  // small FP64 product out = S^-1 v (v, out in shared memory)
   auto small64 = [&](const double *v, double *out) {
-    if (warp == 0) {
-      for (int i = lane; i < nc; i += 32) {
-        double s0 = 0.0, s1 = 0.0;
-        int j = 0;
-        for (; j + 1 < nc; j += 2) {
-          s0 += sinv64[j * nc + i] * v[j];
-          s1 += sinv64[(j + 1) * nc + i] * v[j + 1];
-        }
-        for (; j < nc; ++j) s0 += sinv64[j * nc + i] * v[j];
-        out[i] = s0 + s1;
-      }
+    double s = 0.0;
+    if (srow < nc)
+      for (int j = spart; j < nc; j += KS) s += sinv64[srow * nc + j] * v[j];
+    for (int o = KS >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (spart == 0 && srow < nc) out[srow] = s;
+  };
+  // the CL partial vectors of buffer rb summed into tw[0..cnt) by the CTA (one thread per
+  // entry; the caller synchronises the CTA before tw is read)
+  auto gather_cta = [&](const T *rb, int cnt) {
+    for (int t = tid; t < cnt; t += THREADS) {
+      T v = T(0);
+#pragma unroll
+      for (int rk = 0; rk < CL; ++rk) v += C::remote(rb, rk)[t];
+      tw[t] = v;
     }
+  };
+  // lw = scale S^-1 tw[off ..) (or 0 when zero) by the CTA, rows as in small64
+  auto small_cta = [&](int off, T scale, bool zero) {
+    T s = T(0);
+    if (srow < nc)
+      for (int j = spart; j < nc; j += KS) s += sinv[srow * nc + j] * tw[off + j];
+    for (int o = KS >> 1; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (spart == 0 && srow < nc) lw[srow] = zero ? T(0) : scale * s;
   };
   // inner-precision product lw = scale * S^-1 v (v = tw + off) by every warp for itself;
   // returns scale * lw . v summed over the warp (used by the Jacobi sweep)
@@ -421,14 +440,12 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
     }
     C::sync();
     // mu = S^-1 (g - Ct x)
-    if (warp == 0) {
-      for (int b = lane; b < nc; b += 32) {
-        double s = 0.0;
-        for (int rk = 0; rk < CL; ++rk) s += C::remote(red64, rk)[b];
-        v64[nc + b] = gt[(size_t)b * a.R] - s;
-      }
-      __syncwarp();
+    for (int b = tid; b < nc; b += THREADS) {
+      double s = 0.0;
+      for (int rk = 0; rk < CL; ++rk) s += C::remote(red64, rk)[b];
+      v64[nc + b] = gt[(size_t)b * a.R] - s;
     }
+    __syncthreads();
     small64(v64 + nc, v64);
     __syncthreads();
     // (c) x += M^-1 Ct^T mu
@@ -497,14 +514,12 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
       flush_bins<NC>(rW.acc, rE.acc, red64 + nc, lane, seg, nq, baseW, baseE);
     }
     C::sync();
-    if (warp == 0) {
-      for (int b = lane; b < nc; b += 32) {
-        double s = 0.0;
-        for (int rk = 0; rk < CL; ++rk) s += C::remote(red64, rk)[nc + b];
-        v64[nc + b] = s;
-      }
-      __syncwarp();
+    for (int b = tid; b < nc; b += THREADS) {
+      double s = 0.0;
+      for (int rk = 0; rk < CL; ++rk) s += C::remote(red64, rk)[nc + b];
+      v64[nc + b] = s;
     }
+    __syncthreads();
     small64(v64 + nc, v64);
     __syncthreads();
     // (e) projected residual, its M^-1 norm; the next sweep's residual
@@ -756,10 +771,11 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
         ct_reduce(yv, rr, yv, r2 + 1, r2);
         C::sync();  // B3: sums in place; every CTA has read the previous r1
         for (int t = tid; t < NRED; t += THREADS) r1[t] = T(0);
-        gather(r2, NRED);
+        gather_cta(r2, NRED);
+        __syncthreads();
         const T rho_new = tw[0];
-        small_warp(1, T(1), false);   // lw = mu = S^-1 Ct y
-        __syncwarp();
+        small_cta(1, T(1), false);    // lw = mu = S^-1 Ct y
+        __syncthreads();
         int stop = 0;
         if (!(rho_new >= T(0)) || !(rho_new < T(3.0e38))) stop = 2;
         else if (it == 0) {
@@ -833,13 +849,14 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
         // every CTA read r2 (after B3) before B1, so it can be cleared for the next use
         for (int t = tid; t < NRED; t += THREADS) r2[t] = T(0);
         C::sync();  // B2
-        gather(r1, NRED);
+        gather_cta(r1, NRED);
+        __syncthreads();
         const T tpq = tw[0];
         T alpha = rho / tpq;
         const bool bad = !(tpq > T(0)) || !(alpha == alpha) || !(alpha < T(3.0e38));
         if (bad) alpha = T(0);
-        small_warp(1, alpha, bad);    // lw = lambda = alpha S^-1 Ct M^-1 q
-        __syncwarp();
+        small_cta(1, alpha, bad);     // lw = lambda = alpha S^-1 Ct M^-1 q
+        __syncthreads();
         {
           T wprev = lw[lb[0] * nq + baseW] + lw[lb[dEc] * nq + baseE];
 #pragma unroll
@@ -885,7 +902,7 @@ constexpr size_t level_smem_bytes(int nc) {
   const int nred = NCH > 1 ? 1 + nc : 4 + 2 * nc;
   return sizeof(double) * ((size_t)nc * nc + 2 * nc + 1 + 2 * nc + (SR ? ROWS * W : 0)) +
          sizeof(T) * ((size_t)(NCH > 1 ? 3 : 1) * (ROWS + 2) * W + (ROWS + 1) * NEL + nc * nc +
-                      2 * nred + (THREADS / 32) * (nred + nc) + ROWS * W + 32) +
+                      2 * nred + (NCH > 1 ? 1 : THREADS / 32) * (nred + nc) + ROWS * W + 32) +
          (size_t)(ROWS + 1) * NEL;
 }
 
