@@ -83,32 +83,45 @@ struct ClusterOps {
 
 // Adds a node value to the per-label west/east slots of its four adjacent elements; the
 // north elements of an aligned strip's last row (to_next) go to `bins` directly.
-// Per-label sums of one element column of a strip: a running sum for the current label that
-// goes to the label's slot when the label changes (labels change rarely along a strip), so a
-// value costs one add instead of NC predicated adds. Used for the FP64 constraint sums of the
-// refinement steps, whose FP64 adds run at a small fraction of the FP32 rate.
-template <int NC, typename V>
-struct LabRun {
-  V acc[NC];
-  V cur;
-  int lab;
-  __device__ __forceinline__ void init(int l) {
+// Per-label sums over the element rows of a column strip of the node-pair sums
+// v_(i-1) + v_i, for the west and the east element of the column at once, from one running
+// prefix Q of the node values: a run of element rows s..e with one label adds
+// (Q_e + Q_(e-1)) - (Q_(s-1) + Q_(s-2)), so a node costs one add instead of three (used for
+// the FP64 sums of the refinement steps, whose FP64 adds run at a small fraction of the FP32
+// rate). Element row i lies between node rows i-1 and i; node row -1 belongs to the strip
+// below (its value is added there), so Q starts at zero.
+template <int NC>
+struct PairRuns {
+  double aW[NC], aE[NC];
+  double q1, q2;   // Q_(i-1), Q_(i-2)
+  double sW, sE;   // Q_(s-1) + Q_(s-2) where the current west / east run started
+  int lW, lE;      // labels of the current runs
+  __device__ __forceinline__ void init(int lw, int le) {
 #pragma unroll
-    for (int j = 0; j < NC; ++j) acc[j] = V(0);
-    cur = V(0);
-    lab = l;
+    for (int j = 0; j < NC; ++j) aW[j] = aE[j] = 0.0;
+    q1 = q2 = sW = sE = 0.0;
+    lW = lw;
+    lE = le;
   }
-  __device__ __forceinline__ void add(int l, V v) {
-    if (l != lab) {
-      add_lab<NC>(acc, lab, cur);
-      cur = V(0);
-      lab = l;
+  // element row i, labels (lw, le), gets v_(i-1) + v_i
+  __device__ __forceinline__ void step(int lw, int le, double v) {
+    if (lw != lW) {
+      add_lab<NC>(aW, lW, (q1 + q2) - sW);
+      sW = q1 + q2;
+      lW = lw;
     }
-    cur += v;
+    if (le != lE) {
+      add_lab<NC>(aE, lE, (q1 + q2) - sE);
+      sE = q1 + q2;
+      lE = le;
+    }
+    q2 = q1;
+    q1 += v;
   }
   __device__ __forceinline__ void close() {
-    add_lab<NC>(acc, lab, cur);
-    cur = V(0);
+    const double t = q1 + q2;
+    add_lab<NC>(aW, lW, t - sW);
+    add_lab<NC>(aE, lE, t - sE);
   }
 };
 
@@ -405,38 +418,29 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
 
   for (int step = 0;; ++step) {
     // ================= FP64 refinement step =================
-    // (a) fold the correction; (b) Ct x by element rows (column sums of node pairs)
-    {
-      int lS0 = lb[0], lS1 = lb[dEc];
-      LabRun<NC, double> rW, rE;
-      rW.init(lS0);
-      rE.init(lS1);
+    // (a) fold the correction; (b) Ct x by element rows (column sums of node pairs). The
+    // first step starts from x = 0, where both are zero.
+    if (step > 0) {
+      PairRuns<NC> pr;
+      pr.init(lb[0], lb[dEc]);
       double vprev = 0.0;
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
-        const int lN0 = lb[(i + 1) * NEL], lN1 = lb[(i + 1) * NEL + dEc];
         double v = 0.0;
         if (i < nact) {
           v = xb[i * XW] + (double)x[i];
           xb[i * XW] = v;
         }
         x[i] = T(0);
-        const double u = v + vprev;
-        rW.add(lS0, u);
-        rE.add(lS1, u);
+        pr.step(lb[i * NEL], lb[i * NEL + dEc], v);
         vprev = v;
-        lS0 = lN0;
-        lS1 = lN1;
       }
-      if (!next_row) {
-        rW.add(lS0, vprev);
-        rE.add(lS1, vprev);
-      }
-      flush_next<NC>(next_row && nact == RPT, lS0, lS1, vprev, red64, lane, seg, nq,
+      const int lT0 = lb[RPT * NEL], lT1 = lb[RPT * NEL + dEc];
+      if (!next_row) pr.step(lT0, lT1, 0.0);
+      flush_next<NC>(next_row && nact == RPT, lT0, lT1, vprev, red64, lane, seg, nq,
                      baseWn, baseEn);
-      rW.close();
-      rE.close();
-      flush_bins<NC>(rW.acc, rE.acc, red64, lane, seg, nq, baseW, baseE);
+      pr.close();
+      flush_bins<NC>(pr.aW, pr.aE, red64, lane, seg, nq, baseW, baseE);
     }
     C::sync();
     // mu = S^-1 (g - Ct x)
@@ -471,10 +475,9 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
       double xE0 = any ? xb[-XW + dEx] : 0.0, xW1 = any ? xb[-1] : 0.0;
       double xC1 = any ? xb[0] : 0.0, xE1 = any ? xb[dEx] : 0.0;
       double kS0 = any ? kg[0] : 0.0, kS1 = any ? kg[dEc] : 0.0;
-      int lS0 = lb[0], lS1 = lb[dEc];
-      LabRun<NC, double> rW, rE;
-      rW.init(lS0);
-      rE.init(lS1);
+      double sS = kS0 + kS1;      // kappa sum of the south element pair (the previous north)
+      PairRuns<NC> pr;
+      pr.init(lb[0], lb[dEc]);
       double zprev = 0.0;
 #pragma unroll
       for (int i = 0; i < RPT; ++i) {
@@ -486,32 +489,30 @@ __global__ void __launch_bounds__(NEL * RG, MINB) k_level2d(LevelArgs<T> a) {
           xE2 = xb[(i + 1) * XW + dEx];
         }
         const double kN0 = act ? kg[(i + 1) * n] : 0.0, kN1 = act ? kg[(i + 1) * n + dEc] : 0.0;
-        const int lN0 = lb[(i + 1) * NEL], lN1 = lb[(i + 1) * NEL + dEc];
+        const double sN = kN0 + kN1;
         double zm = 0.0;
         if (act) {
-          const double ax = q1_apply(kS0, kS1, kN0, kN1, xW0, xC0, xE0, xW1, xC1, xE1, xW2, xC2, xE2);
-          const double rv = (bg ? bg[i * XW] : 0.0) - ax;
+          // the Q1 stencil (as q1_apply) with the element-pair kappa sums carried over rows
+          const double t = 4.0 * (sS + sN) * xC1 - (kS1 + kN1) * xE1 - (kS0 + kN0) * xW1 -
+                           sN * xC2 - sS * xC0 -
+                           2.0 * (kN1 * xE2 + kN0 * xW2 + kS1 * xE0 + kS0 * xW0);
+          const double rv = (bg ? bg[i * XW] : 0.0) - t * (1.0 / 6.0);
           if constexpr (SR) rs[(g * RPT + i) * W + kx] = rv;
           else if (r64g) r64g[kx + XW * (ky0 + i)] = rv;
           zm = mg[i * XW] * rv;
         }
-        const double u = zm + zprev;
-        rW.add(lS0, u);
-        rE.add(lS1, u);
+        pr.step(lb[i * NEL], lb[i * NEL + dEc], zm);
         zprev = zm;
         xW0 = xW1; xC0 = xC1; xE0 = xE1;
         xW1 = xW2; xC1 = xC2; xE1 = xE2;
-        kS0 = kN0; kS1 = kN1; lS0 = lN0; lS1 = lN1;
+        kS0 = kN0; kS1 = kN1; sS = sN;
       }
-      if (!next_row) {
-        rW.add(lS0, zprev);
-        rE.add(lS1, zprev);
-      }
-      flush_next<NC>(next_row && nact == RPT, lS0, lS1, zprev, red64 + nc, lane, seg, nq,
+      const int lT0 = lb[RPT * NEL], lT1 = lb[RPT * NEL + dEc];
+      if (!next_row) pr.step(lT0, lT1, 0.0);
+      flush_next<NC>(next_row && nact == RPT, lT0, lT1, zprev, red64 + nc, lane, seg, nq,
                      baseWn, baseEn);
-      rW.close();
-      rE.close();
-      flush_bins<NC>(rW.acc, rE.acc, red64 + nc, lane, seg, nq, baseW, baseE);
+      pr.close();
+      flush_bins<NC>(pr.aW, pr.aE, red64 + nc, lane, seg, nq, baseW, baseE);
     }
     C::sync();
     for (int b = tid; b < nc; b += THREADS) {
