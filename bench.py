@@ -415,8 +415,8 @@ class GpuRun:
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(steps)]
         L = self.L
-        lv = [{"pcg_ms": 0.0, "node_iters": 0, "node_applies": 0, "launches": 0}
-              for _ in range(L)]
+        lv = [{"pcg_ms": 0.0, "node_iters": 0, "node_applies": 0, "launches": 0,
+               "setup_ms": 0.0, "interp_ms": 0.0, "final_ms": 0.0} for _ in range(L)]
         launches = 0
         relres = 0.0
         with ClockSampler(self.dev.index or 0) as clk:
@@ -429,6 +429,8 @@ class GpuRun:
                 for lev in range(1, L + 1):
                     st = self.s.stats(lev)
                     lv[lev - 1]["pcg_ms"] += st["pcg_ms"]
+                    for key in ("setup_ms", "interp_ms", "final_ms"):
+                        lv[lev - 1][key] += st[key]
                     lv[lev - 1]["node_iters"] += st["pcg_node_iters"]
                     lv[lev - 1]["node_applies"] += st["pcg_node_applies"]
                     lv[lev - 1]["launches"] += st["pcg_launches"]
@@ -485,7 +487,13 @@ def roofline(wl, R, t, steps, tiles):
             tot_bytes += b
             by_level.append({"n": n, "ms_per_step": l["pcg_ms"] / steps,
                              "gbs": (b / (l["pcg_ms"] / 1e3) / 1e9) if l["pcg_ms"] > 0 else None,
-                             "launches_per_step": l["launches"] / steps})
+                             "launches_per_step": l["launches"] / steps,
+                             # the level's other phases (library event timing, ms per step):
+                             # constraint data (on the side stream, overlapping earlier
+                             # levels), level-1-grid interpolation and right-hand sides, and
+                             # coefficients plus cell-function assembly
+                             "other_ms": {k[:-3]: l.get(k, 0.0) / steps
+                                          for k in ("setup_ms", "interp_ms", "final_ms")}})
         gbs = tot_bytes / (pcg_ms / 1e3) / 1e9 if pcg_ms > 0 else None
         flops = sum(l["node_applies"] for l in t["levels"]) * FLOPS_PER_NODE_APPLY
         tfl = flops / (pcg_ms / 1e3) / 1e12 if pcg_ms > 0 else None

@@ -135,6 +135,7 @@ struct F64S {
   __device__ static V ld(const double *b, size_t v, int nv, int k) { return b[v * nv + k]; }
   __device__ static void st(double *b, size_t v, int nv, int k, V x) { b[v * nv + k] = x; }
   __device__ static V from(double d) { return d; }
+  __device__ static V fromf(float f) { return (double)f; }
   __device__ static double to(V x) { return x; }
   __device__ static V zero() { return 0.0; }
   __device__ static V shfl_xor(V v, int o) { return __shfl_xor_sync(0xffffffffu, v, o); }
@@ -161,6 +162,7 @@ struct FFS {
   __device__ static V ld(const double *b, size_t v, int nv, int k) { return ff_load(b, v, nv, k); }
   __device__ static void st(double *b, size_t v, int nv, int k, V x) { ff_store(b, v, nv, k, x); }
   __device__ static V from(double d) { return ff_from(d); }
+  __device__ static V fromf(float f) { return ff{f, 0.f}; }
   __device__ static double to(V x) { return ff_to(x); }
   __device__ static V zero() { return ff{0.f, 0.f}; }
   __device__ static V shfl_xor(V v, int o) {

@@ -46,8 +46,9 @@ constexpr int CF_BR = 16;   // fine rows per band
 // A_1 x at a level-1 node: the Q1 stencil (element matrix entries 2/3 on the diagonal, -1/6
 // for an edge neighbour, -1/3 for the opposite corner; h^(d-2) = 1 in 2D) from the kappa of
 // the node's four elements (a SW, b SE, c NW, d NE) and the 3x3 values around it (tr points
-// at the node, rows W apart), as one sum of nine products: 4 (a+b+c+d) x0 - (b+d) xE - (a+c) xW - (c+d) xN - (a+b) xS
-// - 2 (d xNE + c xNW + b xSE + a xSW), times 1/6.
+// at the node, rows W apart), as one sum of nine products:
+//   4 (a+b+c+d) x0 - (b+d) xE - (a+c) xW - (c+d) xN - (a+b) xS
+//   - 2 (d xNE + c xNW + b xSE + a xSW), times 1/6.
 template <class S>
 __device__ __forceinline__ typename S::V q1_dot(typename S::V a, typename S::V b,
                                                 typename S::V c, typename S::V d,
@@ -69,7 +70,7 @@ __device__ __forceinline__ typename S::V q1_dot(typename S::V a, typename S::V b
 }
 
 template <int NC, class S>
-__global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
+__global__ void __launch_bounds__(CF_THREADS, 4) k_child_fine2d(ChildArgs a) {
   using V = typename S::V;
   const int unit = blockIdx.y;
   const int pt = unit / a.R, r = unit % a.R;
@@ -107,8 +108,14 @@ __global__ void __launch_bounds__(CF_THREADS) k_child_fine2d(ChildArgs a) {
       V v = S::zero();
       if (row >= 0 && row <= nf) {
         const int k = col + W * row;
+        // the (at most four) parents' loads are issued together
+        V pv[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) pv[s] = s < ns ? S::ldv(pp[s], a.nvf, k) : S::zero();
         typename S::D acc = S::dzero();
-        for (int s = 0; s < ns; ++s) S::dadd(acc, pw[s], S::ldv(pp[s], a.nvf, k));
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          if (s < ns) S::dadd(acc, pw[s], pv[s]);
         v = S::dget(acc);
       }
       tile[t] = v;
@@ -292,30 +299,49 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram2d(int nv, int slices, const
 
 // b = scale * P^T y on the level grid (zero on its boundary nodes): P^T sums the fine values
 // around coarse node K with the separable hat weights (RHO - |d|) / RHO per axis. One CTA per
-// (unit, KB coarse rows): the fine rows those coarse rows reach are staged in shared memory
-// with coalesced loads, then summed along y per fine column and along x per coarse node.
+// (unit, 32 / RHO coarse rows): the fine rows those coarse rows reach (32 + RHO - 1) are
+// staged in shared memory with coalesced loads, so a fine row is read about once, then summed
+// along y per fine column and along x per coarse node (sums of products as in the Gram).
+constexpr int RS_FINE_ROWS = 32;
+
+template <int RHO>
+constexpr int restrict_rows() { return (RS_FINE_ROWS / RHO - 1) * RHO + 2 * RHO - 1; }
+
 template <int RHO, class S>
 __global__ void __launch_bounds__(256) k_restrict2d(int nf, const double *yf, int nvf,
                                                      double scale, double *outc, int nvc) {
   using V = typename S::V;
-  constexpr int KB = RHO >= 8 ? 1 : 8 / RHO;           // coarse rows per CTA
-  constexpr int NR = (KB - 1) * RHO + 2 * RHO - 1;     // staged fine rows
-  __shared__ V rows[NR * 257];
-  __shared__ V cs[257];
+  constexpr int KB = RS_FINE_ROWS / RHO;               // coarse rows per CTA
+  constexpr int NR = restrict_rows<RHO>();             // staged fine rows
+  extern __shared__ __align__(16) unsigned char rs_smem[];
+  V *rows = reinterpret_cast<V *>(rs_smem);            // [NR][257]
+  V *cs = rows + NR * 257;                             // [257]
   const int unit = blockIdx.y, tid = threadIdx.x;
   const int ncg = nf / RHO, Wc = ncg + 1, Wf = nf + 1;
   const int K0 = blockIdx.x * KB;
   const int fr0 = K0 * RHO - (RHO - 1);                // first staged fine row (may be < 0)
   const typename S::P yb = S::vec(yf, unit, nvf);
   {
-    int fr = fr0 + tid / Wf, col = tid % Wf;          // advanced without divisions
-    for (int t = tid; t < NR * Wf; t += 256) {
-      rows[t] = (fr >= 0 && fr <= nf) ? S::ldv(yb, nvf, fr * Wf + col) : S::zero();
-      col += 256;
-      while (col >= Wf) {
-        col -= Wf;
-        ++fr;
+    // NB loads in flight per thread before their shared-memory stores; (fine row, column)
+    // advanced without divisions
+    constexpr int NB = 8;
+    int fr = fr0 + tid / Wf, col = tid % Wf;
+    for (int t0 = tid; t0 < NR * Wf; t0 += 256 * NB) {
+      V buf[NB];
+#pragma unroll
+      for (int j = 0; j < NB; ++j) {
+        const int t = t0 + 256 * j;
+        buf[j] = (t < NR * Wf && fr >= 0 && fr <= nf) ? S::ldv(yb, nvf, fr * Wf + col)
+                                                       : S::zero();
+        col += 256;
+        while (col >= Wf) {
+          col -= Wf;
+          ++fr;
+        }
       }
+#pragma unroll
+      for (int j = 0; j < NB; ++j)
+        if (t0 + 256 * j < NR * Wf) rows[t0 + 256 * j] = buf[j];
     }
   }
   __syncthreads();
@@ -329,22 +355,23 @@ __global__ void __launch_bounds__(256) k_restrict2d(int nf, const double *yf, in
     }
     for (int col = tid; col < Wf; col += 256) {
       const V *rc = rows + (kk * RHO) * Wf + col;      // fine row Ky RHO - (RHO - 1)
-      V sy = S::zero();
+      typename S::D sy = S::dzero();
 #pragma unroll
       for (int d = 0; d < 2 * RHO - 1; ++d)
-        sy += rc[d * Wf] * float(RHO - (d < RHO - 1 ? RHO - 1 - d : d - (RHO - 1)));
-      cs[col] = sy;
+        S::dadd(sy, rc[d * Wf],
+                S::fromf(float(RHO - (d < RHO - 1 ? RHO - 1 - d : d - (RHO - 1)))));
+      cs[col] = S::dget(sy);
     }
     __syncthreads();
     for (int Kx = tid; Kx < Wc; Kx += 256) {
       double v = 0.0;
       if (Kx > 0 && Kx < ncg) {
         const V *cc = cs + Kx * RHO - (RHO - 1);
-        V sx = S::zero();
+        typename S::D sx = S::dzero();
 #pragma unroll
         for (int d = 0; d < 2 * RHO - 1; ++d)
-          sx += cc[d] * float(RHO - (d < RHO - 1 ? RHO - 1 - d : d - (RHO - 1)));
-        v = scale * S::to(sx) * (1.0 / (RHO * RHO));
+          S::dadd(sx, cc[d], S::fromf(float(RHO - (d < RHO - 1 ? RHO - 1 - d : d - (RHO - 1)))));
+        v = scale * S::to(S::dget(sx)) * (1.0 / (RHO * RHO));
       }
       o[Ky * Wc + Kx] = v;
     }
@@ -370,21 +397,35 @@ __global__ void __launch_bounds__(256) k_prolong_add2d(int nf, const double *xc,
   for (int t = tid; t < (kb + 1) * Wc; t += 256) xs[t] = S::from(x[t]);
   __syncthreads();
   const typename S::P pf = S::vec(phif, unit, nvf);
+  // at most 8 fine rows x 256 columns: PB nodes per thread, all loaded before any store so
+  // that the loads are in flight together
+  constexpr int PB = 8;
+  const int total = kb * RHO * nf;
   int jr = tid / nf, col = tid % nf;                  // fine row K0 RHO + jr, column col
-  for (int t = tid; t < kb * RHO * nf; t += 256) {
-    const int kr = jr / RHO, j = jr % RHO;
-    const int Kx = col / RHO, i = col % RHO;
-    const V *xr = xs + kr * Wc + Kx;
-    const V x00 = xr[0], x10 = xr[1], x01 = xr[Wc], x11 = xr[Wc + 1];
-    const float ty = float(j) * (1.0f / RHO);          // exact: RHO is a power of two
-    const V aj = x00 + (x01 - x00) * ty, bj = x10 + (x11 - x10) * ty;
-    const int k = (K0 * RHO + jr) * Wf + col;
-    S::stv(pf, nvf, k, S::ldv(pf, nvf, k) + (aj + (bj - aj) * (float(i) * (1.0f / RHO))));
+  int kk[PB], jj[PB], cc[PB];
+  V old[PB];
+#pragma unroll
+  for (int u = 0; u < PB; ++u) {
+    jj[u] = jr;
+    cc[u] = col;
+    kk[u] = (K0 * RHO + jr) * Wf + col;
+    old[u] = tid + 256 * u < total ? S::ldv(pf, nvf, kk[u]) : S::zero();
     col += 256;
     while (col >= nf) {
       col -= nf;
       ++jr;
     }
+  }
+#pragma unroll
+  for (int u = 0; u < PB; ++u) {
+    if (tid + 256 * u >= total) break;
+    const int kr = jj[u] / RHO, j = jj[u] % RHO;
+    const int Kx = cc[u] / RHO, i = cc[u] % RHO;
+    const V *xr = xs + kr * Wc + Kx;
+    const V x00 = xr[0], x10 = xr[1], x01 = xr[Wc], x11 = xr[Wc + 1];
+    const float ty = float(j) * (1.0f / RHO);          // exact: RHO is a power of two
+    const V aj = x00 + (x01 - x00) * ty, bj = x10 + (x11 - x10) * ty;
+    S::stv(pf, nvf, kk[u], old[u] + (aj + (bj - aj) * (float(i) * (1.0f / RHO))));
   }
 }
 
@@ -452,15 +493,21 @@ template <class S>
 cudaError_t restrict_s(int npts, int R, int nf, int rho, const double *yf, int nvf, double scale,
                        double *outc, int nvc, cudaStream_t st) {
   if (nf > 256) return cudaErrorInvalidValue;
-  const int Wc = nf / rho + 1, kb = rho >= 8 ? 1 : 8 / rho;
+  const int Wc = nf / rho + 1, kb = RS_FINE_ROWS / rho;
   dim3 grid((Wc + kb - 1) / kb, npts * R);
+  auto run = [&](auto kern, int nr) {
+    const int smem = (nr + 1) * 257 * (int)sizeof(typename S::V);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 256, smem, st>>>(nf, yf, nvf, scale, outc, nvc);
+    return cudaGetLastError();
+  };
   switch (rho) {
-    case 2: k_restrict2d<2, S><<<grid, 256, 0, st>>>(nf, yf, nvf, scale, outc, nvc); break;
-    case 4: k_restrict2d<4, S><<<grid, 256, 0, st>>>(nf, yf, nvf, scale, outc, nvc); break;
-    case 8: k_restrict2d<8, S><<<grid, 256, 0, st>>>(nf, yf, nvf, scale, outc, nvc); break;
+    case 2: return run(k_restrict2d<2, S>, restrict_rows<2>());
+    case 4: return run(k_restrict2d<4, S>, restrict_rows<4>());
+    case 8: return run(k_restrict2d<8, S>, restrict_rows<8>());
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_restrict2d(int npts, int R, int nf, int rho, const double *yf, int nvf,
