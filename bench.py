@@ -523,7 +523,9 @@ def roofline(wl, R, t, steps, tiles):
     for k, l in enumerate(t["levels"]):
         by_level.append({"n": wl.n_level(k + 1), "ms_per_step": l["pcg_ms"] / steps,
                          "gbs": (l["node_iters"] * bpn / (l["pcg_ms"] / 1e3) / 1e9)
-                         if l["pcg_ms"] > 0 else None})
+                         if l["pcg_ms"] > 0 else None,
+                         "other_ms": {k_[:-3]: l.get(k_, 0.0) / steps
+                                      for k_ in ("setup_ms", "interp_ms", "final_ms")}})
     gbs = node_iters * bpn / (pcg_ms / 1e3) / 1e9 if pcg_ms > 0 else None
     return {"bound": "hbm", "kernel": "k_level3d (cooperative level solve)",
             "achieved": gbs, "peak": hbm, "unit": "GB/s",

@@ -120,8 +120,10 @@ __global__ void __launch_bounds__(F3_THREADS) k_interp3d(ChildArgs a) {
 
 // y = h_f A_1 phi and g -= s C_1 phi: one thread per interior node column of the level-1
 // lattice, walking z with sliding windows; the constraint functionals go per (element
-// column, label) into registers, per CTA into shared memory, then into g.
-template <int NCN, class S>
+// column, label) into registers, per CTA into shared memory, then into g. OVS: also the
+// stencil restricted to R_p (oversampling); a separate instantiation, so that the common
+// case keeps its registers (two resident CTAs per SM).
+template <int NCN, class S, bool OVS>
 __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double hf) {
   using V = typename S::V;
   const int unit = blockIdx.y, pt = unit / a.R, r = unit % a.R;
@@ -197,7 +199,7 @@ __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double
       load_k(kk[1], up, kz);
       const V val = v[1][1][1];
       S::st(a.y, unit, a.nvf, (int)(base + W2 * kz), hv * q1_apply3d_v<V>(v, kk, third, twelfth));
-      if (a.yR) {
+      if constexpr (OVS) {
         V kr[2][2][2];
 #pragma unroll
         for (int sz = 0; sz < 2; ++sz)
@@ -571,12 +573,14 @@ cudaError_t launch_fine_apply3d(const ChildArgs &a, double hf, cudaStream_t st, 
   if (a.nc > MCH_MAX_NC3 || (ffs && !a.kappa_ff)) return cudaErrorInvalidValue;
   const int ni = a.nf - 1;
   dim3 grid((ni * ni + F3_THREADS - 1) / F3_THREADS, a.npts * a.R);
+  auto go = [&](auto kern) { kern<<<grid, F3_THREADS, 0, st>>>(a, hf); };
+  const bool ovs = a.yR != nullptr;
   if (ffs) {
-    if (a.N <= 2) k_fine_apply3d<2, FFS><<<grid, F3_THREADS, 0, st>>>(a, hf);
-    else k_fine_apply3d<4, FFS><<<grid, F3_THREADS, 0, st>>>(a, hf);
+    if (a.N <= 2) ovs ? go(k_fine_apply3d<2, FFS, true>) : go(k_fine_apply3d<2, FFS, false>);
+    else ovs ? go(k_fine_apply3d<4, FFS, true>) : go(k_fine_apply3d<4, FFS, false>);
   } else {
-    if (a.N <= 2) k_fine_apply3d<2, F64S><<<grid, F3_THREADS, 0, st>>>(a, hf);
-    else k_fine_apply3d<4, F64S><<<grid, F3_THREADS, 0, st>>>(a, hf);
+    if (a.N <= 2) ovs ? go(k_fine_apply3d<2, F64S, true>) : go(k_fine_apply3d<2, F64S, false>);
+    else ovs ? go(k_fine_apply3d<4, F64S, true>) : go(k_fine_apply3d<4, F64S, false>);
   }
   return cudaGetLastError();
 }
