@@ -123,8 +123,8 @@ __global__ void __launch_bounds__(F3_THREADS) k_interp3d(ChildArgs a) {
 // column, label) into registers, per CTA into shared memory, then into g. OVS: also the
 // stencil restricted to R_p (oversampling); a separate instantiation, so that the common
 // case keeps its registers (two resident CTAs per SM).
-template <int NCN, class S, bool OVS>
-__global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double hf) {
+template <class S, bool OVS>
+__global__ void __launch_bounds__(F3_THREADS, 2) k_fine_apply3d(ChildArgs a, double hf) {
   using V = typename S::V;
   const int unit = blockIdx.y, pt = unit / a.R, r = unit % a.R;
   const int nf = a.nf, W = nf + 1, ni = nf - 1, lgr = a.lgr, ncg = nf >> lgr;
@@ -168,24 +168,57 @@ __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double
     load_v(v[0], 0);
     load_v(v[1], 1);
     load_k(kk[0], lo, 0);
-    V acc[4][NCN];
+    // kappa pair sums of the element plane below the node (carried over from the step
+    // before): along x per element row oy, along y per element column ox, and the plane's sum
+    V px0[2], py0[2], ps0;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      px0[i] = kk[0][i][0] + kk[0][i][1];
+      py0[i] = kk[0][0][i] + kk[0][1][i];
+    }
+    ps0 = px0[0] + px0[1];
+    const V hv12 = S::from(hf / 12.0);
+    // C_1 phi: each of the four element columns c = 2 sy + sx around the node column sums,
+    // per (label, z-block), the node pairs (kz, kz+1) of its elements; all four share one
+    // running prefix Q of the column's node values, and a run of elements with one label and
+    // z-block adds (Q_e + Q_(e-1)) - (Q_(s-1) + Q_(s-2)) to its bin when it ends (labels and
+    // z-blocks change rarely along a column), instead of per-node adds into every label slot.
+    int bxy[4];
 #pragma unroll
     for (int c = 0; c < 4; ++c)
+      bxy[c] = ((ky - 1 + (c >> 1)) >> a.lgmf) * P + ((kx - 1 + (c & 1)) >> a.lgmf);
+    V q1 = S::zero(), q2 = S::zero(), rs[4];
+    int rl[4];
 #pragma unroll
-      for (int j = 0; j < NCN; ++j) acc[c][j] = S::zero();
-    int zb = 0;
-    auto flush = [&]() {
+    for (int c = 0; c < 4; ++c) {
+      rs[c] = S::zero();
+      rl[c] = lo[c >> 1][c & 1];
+    }
+    int zoff = 0;  // z-block of the current element plane * P^2
+    auto close = [&](int c) {
+      const double d = S::to((q1 + q2) - rs[c]);
+      if (rl[c] < a.N && d != 0.0) atomicAdd(&bins[rl[c] * nq + zoff + bxy[c]], d);
+      rs[c] = q1 + q2;
+    };
+    // element plane i = kz - 1 (labels lp) gets the next node value through v_next
+    auto elem_plane = [&](int i, const int (&lp)[2][2], V v_next) {
+      if (i > 0 && (i & (mf - 1)) == 0) {
 #pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        const int ex = kx - 1 + (c & 1), ey = ky - 1 + (c >> 1);
-        const int bb = (zb * P + (ey >> a.lgmf)) * P + (ex >> a.lgmf);
-#pragma unroll
-        for (int j = 0; j < NCN; ++j) {
-          const double d = S::to(acc[c][j]);
-          if (d != 0.0) atomicAdd(&bins[j * nq + bb], d);
-          acc[c][j] = S::zero();
+        for (int c = 0; c < 4; ++c) {
+          close(c);
+          rl[c] = lp[c >> 1][c & 1];
         }
+        zoff = (i >> a.lgmf) * P * P;
+      } else {
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          if (lp[c >> 1][c & 1] != rl[c]) {
+            close(c);
+            rl[c] = lp[c >> 1][c & 1];
+          }
       }
+      q2 = q1;
+      q1 = q1 + v_next;
     };
     // oversampling: the same stencil with kappa zero outside R_p (period index of each
     // adjacent fine element)
@@ -197,8 +230,38 @@ __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double
     for (int kz = 1; kz < nf; ++kz) {
       load_v(v[2], kz + 1);
       load_k(kk[1], up, kz);
-      const V val = v[1][1][1];
-      S::st(a.y, unit, a.nvf, (int)(base + W2 * kz), hv * q1_apply3d_v<V>(v, kk, third, twelfth));
+      // the 21-point stencil (k3d.cuh) as one sum of products: 4 ksum x0 minus every
+      // coupling kappa (sum) times its neighbour, over 12
+      V px1[2], py1[2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        px1[i] = kk[1][i][0] + kk[1][i][1];
+        py1[i] = kk[1][0][i] + kk[1][1][i];
+      }
+      const V ps1 = px1[0] + px1[1];
+      typename S::D t = S::dzero();
+      S::dadd(t, S::scale2(ps0 + ps1, 4.f), v[1][1][1]);
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        const int oz = c >> 2, oy = (c >> 1) & 1, ox = c & 1;
+        S::dadd(t, -kk[oz][oy][ox], v[2 * oz][2 * oy][2 * ox]);
+      }
+#pragma unroll
+      for (int oy = 0; oy < 2; ++oy)
+#pragma unroll
+        for (int ox = 0; ox < 2; ++ox)
+          S::dadd(t, -(kk[0][oy][ox] + kk[1][oy][ox]), v[1][2 * oy][2 * ox]);
+#pragma unroll
+      for (int ox = 0; ox < 2; ++ox) {
+        S::dadd(t, -py0[ox], v[0][1][2 * ox]);
+        S::dadd(t, -py1[ox], v[2][1][2 * ox]);
+      }
+#pragma unroll
+      for (int oy = 0; oy < 2; ++oy) {
+        S::dadd(t, -px0[oy], v[0][2 * oy][1]);
+        S::dadd(t, -px1[oy], v[2][2 * oy][1]);
+      }
+      S::st(a.y, unit, a.nvf, (int)(base + W2 * kz), S::dget(t) * hv12);
       if constexpr (OVS) {
         V kr[2][2][2];
 #pragma unroll
@@ -212,20 +275,7 @@ __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double
         S::st(a.yR, unit, a.nvf, (int)(base + W2 * kz),
               hv * q1_apply3d_v<V>(v, kr, third, twelfth));
       }
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int j = 0; j < NCN; ++j)
-          if (lo[c >> 1][c & 1] == j) acc[c][j] += val;
-      if ((kz & (mf - 1)) == 0) {
-        flush();
-        zb = kz / mf;
-      }
-#pragma unroll
-      for (int c = 0; c < 4; ++c)
-#pragma unroll
-        for (int j = 0; j < NCN; ++j)
-          if (up[c >> 1][c & 1] == j) acc[c][j] += val;
+      elem_plane(kz - 1, lo, v[1][1][1]);
 #pragma unroll
       for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -240,8 +290,17 @@ __global__ void __launch_bounds__(F3_THREADS) k_fine_apply3d(ChildArgs a, double
           kk[0][i][j] = kk[1][i][j];
           lo[i][j] = up[i][j];
         }
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        px0[i] = px1[i];
+        py0[i] = py1[i];
+      }
+      ps0 = ps1;
     }
-    flush();
+    // the top element plane nf - 1 (its upper nodes are boundary nodes, value 0)
+    elem_plane(nf - 1, lo, S::zero());
+#pragma unroll
+    for (int c = 0; c < 4; ++c) close(c);
   }
   __syncthreads();
   double *g = a.g + (size_t)pt * a.nc * a.R + r;
@@ -575,13 +634,8 @@ cudaError_t launch_fine_apply3d(const ChildArgs &a, double hf, cudaStream_t st, 
   dim3 grid((ni * ni + F3_THREADS - 1) / F3_THREADS, a.npts * a.R);
   auto go = [&](auto kern) { kern<<<grid, F3_THREADS, 0, st>>>(a, hf); };
   const bool ovs = a.yR != nullptr;
-  if (ffs) {
-    if (a.N <= 2) ovs ? go(k_fine_apply3d<2, FFS, true>) : go(k_fine_apply3d<2, FFS, false>);
-    else ovs ? go(k_fine_apply3d<4, FFS, true>) : go(k_fine_apply3d<4, FFS, false>);
-  } else {
-    if (a.N <= 2) ovs ? go(k_fine_apply3d<2, F64S, true>) : go(k_fine_apply3d<2, F64S, false>);
-    else ovs ? go(k_fine_apply3d<4, F64S, true>) : go(k_fine_apply3d<4, F64S, false>);
-  }
+  if (ffs) ovs ? go(k_fine_apply3d<FFS, true>) : go(k_fine_apply3d<FFS, false>);
+  else ovs ? go(k_fine_apply3d<F64S, true>) : go(k_fine_apply3d<F64S, false>);
   return cudaGetLastError();
 }
 
