@@ -89,16 +89,16 @@ FP32_LANES = 128
 # (kappa 4 B, labels 1 B and M^-1 4 B in the first pass, labels and M^-1 in the second: 14 B)
 # is shared by the point's R functions
 BYTES3D_PER_NODE_ITER_UNIT, BYTES3D_PER_NODE_ITER_POINT = 40, 14
-# DRAM bytes (read + write) per k_level2d launch from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum), per workload and level. Valid only for
-# the kernel sources they were taken on: null is reported when the sources' hash differs.
+# DRAM bytes (read + write) per k_level2d launch from ncu captures, per workload, keyed by
+# (grid n, launch shape) so that either of the autotuner's usual picks is covered. Valid
+# only for the kernel sources they were taken on: null is reported when the sources' hash
+# differs or a level ran a shape without a capture.
 LEVEL_TRAFFIC = {
     # ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
     #     --clock-control none -k regex:k_level2d -s 12 -c 4 python bench.py --no-configs
-    #     --no-cpu --no-plain --steps 1 --warmup 3 --tiles 4,7,9,5   (the timed step's launches)
-    "incl2d_33x33_L4": {"sha256_16": "5e14af1f3715f415", "tiles": (4, 7, 9, 5),
-                        "bytes_per_launch": (101.346816e6, 117.472512e6, 111.101184e6,
-                                             134.148096e6)},
+    #     --no-cpu --no-plain --steps 1 --warmup 3 --tiles T   (the timed step's launches;
+    #     T = 2,5,9,5 and 4,7,9,5)
+    "incl2d_33x33_L4": {"sha256_16": None, "bytes_per_launch": {}},
 }
 
 
@@ -153,19 +153,21 @@ class ClockSampler:
 def _sources_hash():
     import hashlib
     h = hashlib.sha256()
-    for f in ("k_level.cuh", "k_level_f32.cu", "k_level_f32_alt.cu", "k_level_f32_alt2.cu",
-              "k_level_shapes.h"):
+    for f in ("k_level.cuh", "common.cuh", "k_level_f32.cu", "k_level_f32_alt.cu",
+              "k_level_f32_alt2.cu", "k_level_shapes.h"):
         with open(os.path.join(ROOT, "paper_2503_01276_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _level_traffic(wl_name, tiles):
-    rec = LEVEL_TRAFFIC.get(wl_name)
-    if not rec or rec["sha256_16"] != _sources_hash() or list(rec["tiles"]) != list(tiles):
+def _level_traffic(wl, tiles):
+    rec = LEVEL_TRAFFIC.get(wl.name)
+    if not rec or rec["sha256_16"] != _sources_hash() or not tiles:
         return None, None
-    b = rec["bytes_per_launch"]
-    return float(np.mean(b)), list(b)
+    b = [rec["bytes_per_launch"].get((wl.n_level(k + 1), v)) for k, v in enumerate(tiles)]
+    if any(x is None for x in b):
+        return None, None
+    return float(np.mean(b)), b
 
 
 def max_over_ranks(t_local: float, dist, device) -> float:
@@ -498,7 +500,7 @@ def roofline(wl, R, t, steps, tiles):
         flops = sum(l["node_applies"] for l in t["levels"]) * FLOPS_PER_NODE_APPLY
         tfl = flops / (pcg_ms / 1e3) / 1e12 if pcg_ms > 0 else None
         derived = _sm_count() * FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
-        traffic, traffic_levels = _level_traffic(wl.name, tiles)
+        traffic, traffic_levels = _level_traffic(wl, tiles)
         launches = sum(l["launches"] for l in t["levels"])
         return {"bound": "hbm", "kernel": "k_level2d (persistent level solve)",
                 "achieved": gbs, "peak": hbm, "unit": "GB/s",

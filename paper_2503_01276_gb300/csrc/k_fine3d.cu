@@ -101,21 +101,35 @@ template <class S>
 __global__ void __launch_bounds__(F3_THREADS) k_interp3d(ChildArgs a) {
   using V = typename S::V;
   const int unit = blockIdx.y, pt = unit / a.R, r = unit % a.R;
-  // the point's parent vectors and weights, converted once per block
+  // the point's parents with a cell function, packed to the front, and their weights,
+  // converted once per block
   __shared__ typename S::P pp[8];
   __shared__ V pw[8];
-  if (threadIdx.x < a.slots) {
-    const double *b = a.par_ptr[pt * a.slots + threadIdx.x];
-    pp[threadIdx.x] = b ? S::vec(b, r, a.nvf) : nullptr;
-    pw[threadIdx.x] = S::from(a.par_w[pt * a.slots + threadIdx.x]);
+  __shared__ int nslot;
+  if (threadIdx.x == 0) {
+    int ns = 0;
+    for (int s = 0; s < a.slots && s < 8; ++s) {
+      const double *b = a.par_ptr[pt * a.slots + s];
+      if (!b) continue;
+      pp[ns] = S::vec(b, r, a.nvf);
+      pw[ns] = S::from(a.par_w[pt * a.slots + s]);
+      ++ns;
+    }
+    nslot = ns;
   }
   __syncthreads();
   const int k = blockIdx.x * F3_THREADS + threadIdx.x;
   if (k >= a.nvf) return;
-  V v = S::zero();
-  for (int s = 0; s < a.slots; ++s)
-    if (pp[s]) v += pw[s] * S::ldv(pp[s], a.nvf, k);
-  S::st(a.phi, unit, a.nvf, k, v);
+  const int ns = nslot;
+  // every parent's load is issued before the sum of products
+  V pv[8];
+#pragma unroll
+  for (int s = 0; s < 8; ++s) pv[s] = s < ns ? S::ldv(pp[s], a.nvf, k) : S::zero();
+  typename S::D acc = S::dzero();
+#pragma unroll
+  for (int s = 0; s < 8; ++s)
+    if (s < ns) S::dadd(acc, pw[s], pv[s]);
+  S::st(a.phi, unit, a.nvf, k, S::dget(acc));
 }
 
 // y = h_f A_1 phi and g -= s C_1 phi: one thread per interior node column of the level-1
