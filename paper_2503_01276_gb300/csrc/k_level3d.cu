@@ -114,48 +114,79 @@ struct ZBlk {
 };
 
 // Per-column accumulation of node values into the constraint rows of the adjacent elements
-// (node-based form of Ct v): each of the four element columns c = 2 sy + sx around the node
-// column keeps one partial sum for its current label and z-block; a change of label or of
-// z-block flushes it to shared memory (labels change rarely along a column). bxy[c] is the
-// element column's sub-block index within a z-block, zoff the current z-block * P^2.
-template <typename V>
-struct ColBins {
-  V acc[4];
+// (node-based form of Ct v): element plane ez of each of the four element columns c = 2 sy +
+// sx around the node column gets the values of node planes ez and ez + 1. NV value streams
+// share one set of runs: each stream keeps one running prefix Q of the column's node values,
+// and a run of elements with one label and z-block adds (Q_e + Q_(e-1)) - (Q_(s-1) +
+// Q_(s-2)) to shared memory when it ends (labels and z-blocks change rarely along a column),
+// so a node costs one add per stream instead of one per element column. bins[k] is stream
+// k's constraint rows, bxy[c] the element column's sub-block index within a z-block, zoff
+// the current z-block * P^2.
+template <typename V, int NV>
+struct ColRuns {
+  V q1[NV], q2[NV], st[4][NV];
   int lab[4];
-  int zoff;
-  double *bins;
+  int zoff, nq;
+  double *bins[NV];
   const int *bxy;
-  int nq;
-  __device__ __forceinline__ void init(double *b, const int *bxy_, int nq_) {
-    bins = b;
+  // labels of element plane 0
+  __device__ __forceinline__ void init(double *const (&b)[NV], const int *bxy_, int nq_,
+                                       const int (&l)[2][2]) {
     bxy = bxy_;
     nq = nq_;
     zoff = 0;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      acc[c] = V(0);
-      lab[c] = -1;
+    for (int k = 0; k < NV; ++k) {
+      bins[k] = b[k];
+      q1[k] = q2[k] = V(0);
     }
-  }
-  __device__ __forceinline__ void flush_one(int c) {
-    if (lab[c] >= 0 && acc[c] != V(0)) atomicAdd(&bins[lab[c] * nq + zoff + bxy[c]], (double)acc[c]);
-    acc[c] = V(0);
-  }
-  __device__ __forceinline__ void add(const int (&l)[2][2], V v) {
 #pragma unroll
     for (int c = 0; c < 4; ++c) {
-      const int lc = l[c >> 1][c & 1];
-      if (lc != lab[c]) {
-        flush_one(c);
-        lab[c] = lc;
+      lab[c] = l[c >> 1][c & 1];
+#pragma unroll
+      for (int k = 0; k < NV; ++k) st[c][k] = V(0);
+    }
+  }
+  __device__ __forceinline__ void close(int c) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      const V t = q1[k] + q2[k];
+      const V d = t - st[c][k];
+      if (d != V(0)) atomicAdd(&bins[k][lab[c] * nq + zoff + bxy[c]], (double)d);
+      st[c][k] = t;
+    }
+  }
+  // element plane i (labels l, z-block offset zo) gets v, the values of node plane i + 1
+  __device__ __forceinline__ void step(const int (&l)[2][2], int zo, const V (&v)[NV]) {
+    if (zo != zoff) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        close(c);
+        lab[c] = l[c >> 1][c & 1];
       }
-      acc[c] += v;
+      zoff = zo;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 4; ++c)
+        if (l[c >> 1][c & 1] != lab[c]) {
+          close(c);
+          lab[c] = l[c >> 1][c & 1];
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      q2[k] = q1[k];
+      q1[k] += v[k];
     }
   }
-  // all partial sums out (at a z-block boundary and at the end of the column)
-  __device__ __forceinline__ void flush() {
+  // the top element plane (its upper node plane is the boundary, value 0), then every run out
+  __device__ __forceinline__ void finish(const int (&l)[2][2], int zo) {
+    V zero[NV];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) flush_one(c);
+    for (int k = 0; k < NV; ++k) zero[k] = V(0);
+    step(l, zo, zero);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) close(c);
   }
 };
 
@@ -206,8 +237,8 @@ __device__ __forceinline__ void p1_column(const T *__restrict__ p, T *__restrict
                                           const T *__restrict__ rv, const T *__restrict__ mi,
                                           const T *__restrict__ kap,
                                           const uint8_t *__restrict__ lab, int n, int kx, int ky,
-                                          int m, int pp, int nm1, T h, ColBins<T> &bz,
-                                          ColBins<T> &bq, T (&sum)[4]) {
+                                          int m, int pp, int nm1, T h, double *bz,
+                                          double *bq, const int *bxy, int nq, T (&sum)[4]) {
   const int W = n + 1, W2 = W * W;
   T v[3][3][3], k[2][2][2];
   load_plane9(v[0], p, 0, W);
@@ -215,6 +246,8 @@ __device__ __forceinline__ void p1_column(const T *__restrict__ p, T *__restrict
   load_kplane(k[0], kap, kx, ky, 0, n);
   int lo[2][2], up[2][2];
   load_lplane(lo, lab, kx, ky, 0, n, nm1);
+  ColRuns<T, 2> cr;
+  cr.init({bz, bq}, bxy, nq, lo);
   ZBlk zb;
   zb.init(m, pp);
   for (int kz = 1; kz < n; ++kz, zb.next()) {
@@ -230,15 +263,7 @@ __device__ __forceinline__ void p1_column(const T *__restrict__ p, T *__restrict
     sum[1] += z * qv;
     sum[2] += qv * qm;
     sum[3] += r * z;
-    bz.add(lo, z);
-    bq.add(lo, qm);
-    if (zb.boundary()) {
-      bz.flush();
-      bq.flush();
-      bz.zoff = bq.zoff = zb.up;
-    }
-    bz.add(up, z);
-    bq.add(up, qm);
+    cr.step(lo, zb.lo, {z, qm});
 #pragma unroll
     for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -254,8 +279,7 @@ __device__ __forceinline__ void p1_column(const T *__restrict__ p, T *__restrict
         lo[i][j] = up[i][j];
       }
   }
-  bz.flush();
-  bq.flush();
+  cr.finish(lo, zb.lo);
 }
 
 // delta += alpha p; r <- r - alpha q - Ct^T lambda; p = M^-1 r + beta p (unless last).
@@ -448,10 +472,10 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
       if (S.flags[cl.slot] & F_DONE) continue;
       const size_t ub = (size_t)cl.u * a.nv + cl.kx + (size_t)W * cl.ky;
       const uint8_t *lab = a.labels + (size_t)cl.pt * n * n * n;
-      ColBins<double> cb;
-      cb.init(S.bins + cl.slot * 2 * nc, cl.bxy, nq);
       int lo[2][2], up[2][2];
       load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
+      ColRuns<double, 1> cr;
+      cr.init({S.bins + cl.slot * 2 * nc}, cl.bxy, nq, lo);
       ZBlk zb;
       zb.init(m, P * P);
       for (int kz = 1; kz < n; ++kz, zb.next()) {
@@ -463,18 +487,13 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
           a.x[o] = xv;
           a.d[o] = T(0);
         }
-        cb.add(lo, xv);
-        if (zb.boundary()) {
-          cb.flush();
-          cb.zoff = zb.up;
-        }
-        cb.add(up, xv);
+        cr.step(lo, zb.lo, {xv});
 #pragma unroll
         for (int i = 0; i < 2; ++i)
 #pragma unroll
           for (int j = 0; j < 2; ++j) lo[i][j] = up[i][j];
       }
-      cb.flush();
+      cr.finish(lo, zb.lo);
     }
     __syncthreads();
     push_local(nc);
@@ -527,8 +546,8 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
       load_kplane(k[0], kap, cl.kx, cl.ky, 0, n);
       int lo[2][2], up[2][2];
       load_lplane(lo, lab, cl.kx, cl.ky, 0, n, a.N - 1);
-      ColBins<double> cb;
-      cb.init(S.bins + cl.slot * 2 * nc, cl.bxy, nq);
+      ColRuns<double, 1> cr;
+      cr.init({S.bins + cl.slot * 2 * nc}, cl.bxy, nq, lo);
       ZBlk zb;
       zb.init(m, P * P);
       for (int kz = 1; kz < n; ++kz, zb.next()) {
@@ -540,12 +559,7 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
         if (bb) r += bb[o - (size_t)cl.u * a.nv];
         a.r64[o] = r;
         const double mr = a.minv64[mb + W2 * kz] * r;
-        cb.add(lo, mr);
-        if (zb.boundary()) {
-          cb.flush();
-          cb.zoff = zb.up;
-        }
-        cb.add(up, mr);
+        cr.step(lo, zb.lo, {mr});
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
@@ -561,7 +575,7 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
             lo[i][j] = up[i][j];
           }
       }
-      cb.flush();
+      cr.finish(lo, zb.lo);
     }
     __syncthreads();
     push_local(nc);
@@ -649,14 +663,11 @@ __global__ void __launch_bounds__(L3_THREADS, 2) k_level3d(Level3Args<T> a) {
         if (!(S.flags[cl.slot] & F_INNER)) continue;
         const size_t ub = (size_t)cl.u * a.nv + cl.kx + (size_t)W * cl.ky;
         const size_t mb = (size_t)cl.pt * a.nv + cl.kx + (size_t)W * cl.ky;
-        ColBins<T> bz, bq;
         double *sb = S.bins + cl.slot * 2 * nc;
-        bz.init(sb, cl.bxy, nq);
-        bq.init(sb + nc, cl.bxy, nq);
         T sum[4] = {0, 0, 0, 0};
         p1_column<T>(a.p + ub, a.q + ub, a.r + ub, a.minvT + mb,
                      a.kapT + (size_t)cl.pt * n * n * n, a.labels + (size_t)cl.pt * n * n * n, n,
-                     cl.kx, cl.ky, m, P * P, a.N - 1, (T)a.h, bz, bq, sum);
+                     cl.kx, cl.ky, m, P * P, a.N - 1, (T)a.h, sb, sb + nc, cl.bxy, nq, sum);
         const T pq = sum[0], zq = sum[1], qmq = sum[2], rz = sum[3];
         double *ss = S.sums + cl.slot * 8;
         {
