@@ -297,6 +297,99 @@ __global__ void __launch_bounds__(GR_THREADS) k_gram2d(int nv, int slices, const
   }
 }
 
+// The symmetric Gram (Y = A_1 X) in float-float storage with the pairs split over two warp
+// sets: rows r and R-1-r carry R+1 pairs together, and such row pairs alternate between the
+// sets (the middle row of an odd R joins set 0), so a warp keeps about half of the pair sums
+// and loads Y and its own rows of X. Warps 2g and 2g+1 take the same nodes with the two sets:
+// twice the resident warps of k_gram2d at the same loads per pair (the point's R (R+1) / 2
+// pair sums in registers otherwise hold a CTA per SM).
+template <int R>
+struct GramSplit {
+  static constexpr int set_of(int r) { return (r < R - 1 - r ? r : R - 1 - r) & 1; }
+  static constexpr int np(int set) {
+    int c = 0;
+    for (int r = 0; r < R; ++r)
+      if (set_of(r) == set) c += R - r;
+    return c;
+  }
+  static constexpr int NPMAX = np(0) > np(1) ? np(0) : np(1);
+  // index of pair (r, s), r <= s, among its set's pairs, and in the full upper triangle
+  static constexpr int local(int r, int s) {
+    int c = 0;
+    for (int q = 0; q < r; ++q)
+      if (set_of(q) == set_of(r)) c += R - q;
+    return c + (s - r);
+  }
+  static constexpr int global(int r, int s) { return r * R - r * (r - 1) / 2 + (s - r); }
+};
+
+template <int R, class S, int SET>
+__device__ __forceinline__ void gram_split_walk(typename S::D (&acc)[GramSplit<R>::NPMAX],
+                                                typename S::P x0, typename S::P y0, int vstride,
+                                                int nv, int k0, int k1, int node0, int nstep) {
+  using V = typename S::V;
+  using G = GramSplit<R>;
+  for (int k = k0 + node0; k < k1; k += nstep) {
+    V yv[R], xv[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      yv[r] = S::ldv(y0 + r * vstride, nv, k);
+      if (G::set_of(r) == SET) xv[r] = S::ldv(x0 + r * vstride, nv, k);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      if (G::set_of(r) != SET) continue;
+#pragma unroll
+      for (int s = r; s < R; ++s) S::dadd(acc[G::local(r, s)], xv[r], yv[s]);
+    }
+  }
+}
+
+template <int R, class S>
+__global__ void __launch_bounds__(GR_THREADS, 2) k_gram2d_split(int nv, int slices,
+                                                                const double *X, const double *Y,
+                                                                double alpha, double *E) {
+  using V = typename S::V;
+  using G = GramSplit<R>;
+  constexpr int NP = R * (R + 1) / 2;
+  __shared__ double red[GR_THREADS / 32][NP];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < (GR_THREADS / 32) * NP; i += GR_THREADS) (&red[0][0])[i] = 0.0;
+  const int pt = blockIdx.x;
+  const int per = (nv + slices - 1) / slices;
+  const int k0 = blockIdx.y * per, k1 = min(nv, k0 + per);
+  typename S::D acc[G::NPMAX];
+#pragma unroll
+  for (int p = 0; p < G::NPMAX; ++p) acc[p] = S::dzero();
+  const typename S::P x0 = S::vec(X, (size_t)pt * R, nv), y0 = S::vec(Y, (size_t)pt * R, nv);
+  const int vstride = (int)(S::vec(X, 1, nv) - S::vec(X, 0, nv));
+  const int node0 = (w >> 1) * 32 + lane, nstep = GR_THREADS / 2;
+  const int set = w & 1;                                  // uniform over the warp
+  if (set == 0) gram_split_walk<R, S, 0>(acc, x0, y0, vstride, nv, k0, k1, node0, nstep);
+  else gram_split_walk<R, S, 1>(acc, x0, y0, vstride, nv, k0, k1, node0, nstep);
+  __syncthreads();                                        // red zeroed
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int s = r; s < R; ++s) {
+      if (G::set_of(r) != set) continue;
+      const V v = seg_sum_s<S>(S::dget(acc[G::local(r, s)]), 32);
+      if (lane == 0) red[w][G::global(r, s)] = S::to(v);
+    }
+  __syncthreads();
+  for (int p = threadIdx.x; p < NP; p += GR_THREADS) {
+    double sum = 0.0;
+    for (int ww = 0; ww < GR_THREADS / 32; ++ww) sum += red[ww][p];
+    int rr = 0, q = p;
+    while (q >= R - rr) { q -= R - rr; ++rr; }
+    const int cc = rr + q;
+    double *Ep = E + (size_t)pt * R * R;
+    const double v = alpha * sum;
+    atomicAdd(&Ep[rr * R + cc], v);
+    if (cc != rr) atomicAdd(&Ep[cc * R + rr], v);
+  }
+}
+
 // b = scale * P^T y on the level grid (zero on its boundary nodes): P^T sums the fine values
 // around coarse node K with the separable hat weights (RHO - |d|) / RHO per axis. One CTA per
 // (unit, 32 / RHO coarse rows): the fine rows those coarse rows reach (32 + RHO - 1) are
@@ -468,6 +561,17 @@ cudaError_t gram_s(int npts, int R, int nv, const double *X, const double *Y, do
     slices = want < 8 ? 8 : (want > nv / 4096 ? nv / 4096 : want);
   }
   dim3 grid(npts, slices);
+  if constexpr (SYM && std::is_same<S, FFS>::value) {
+    switch (R) {
+      case 3: k_gram2d_split<3, S><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+      case 4: k_gram2d_split<4, S><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+      case 6: k_gram2d_split<6, S><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+      case 8: k_gram2d_split<8, S><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+      case 9: k_gram2d_split<9, S><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
+      default: break;                                   // R = 12: the pair sums do not fit
+    }
+    if (R <= 9) return cudaGetLastError();
+  }
   switch (R) {
     case 3: k_gram2d<3, S, SYM><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
     case 4: k_gram2d<4, S, SYM><<<grid, GR_THREADS, 0, st>>>(nv, slices, X, Y, alpha, E); break;
