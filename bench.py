@@ -98,7 +98,7 @@ LEVEL_TRAFFIC = {
     #     --clock-control none -k regex:k_level2d -s 12 -c 4 python bench.py --no-configs
     #     --no-cpu --no-plain --steps 1 --warmup 3 --tiles T   (the timed step's launches;
     #     T = 2,5,9,5 and 4,7,9,5)
-    "incl2d_33x33_L4": {"sha256_16": "3b841367946e52e3", "bytes_per_launch": {
+    "incl2d_33x33_L4": {"sha256_16": "e75087f419c9503d", "bytes_per_launch": {
         (256, 2): 252.150e6, (128, 5): 209.942e6, (64, 9): 110.006e6, (32, 5): 187.339e6,
         (256, 4): 253.313e6, (128, 7): 211.140e6}},
 }

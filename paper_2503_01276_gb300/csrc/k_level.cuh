@@ -41,9 +41,13 @@
 //       lambda = alpha S^-1 Ct M^-1 q; delta += alpha p; r <- r - alpha q + Ct^T lambda.
 //     The sweep ends when sqrt(rho' / rho_first) < max(tol, 0.3 rtol / ratio), ratio the
 //     refinement step's residual ratio: the last sweep stops once rtol is within reach.
-// Every warp evaluates the scalars and multipliers from the reduced sums itself. Keeping r
-// projected avoids the cancellation that otherwise pushes FP32 iterates off the constraint
-// set; the FP64 steps restore the constraints and the true residual.
+// After a reduction's barrier the scalars and multipliers come from the same summed values
+// everywhere: in the Jacobi sweep every warp evaluates them itself; in the Chebyshev sweep and
+// the refinement steps the CTA gathers the CL partial vectors once and forms the small
+// products S^-1 c cooperatively (a row per power-of-two group of threads), then shares them
+// through shared memory. Keeping r projected avoids the cancellation that otherwise pushes
+// FP32 iterates off the constraint set; the FP64 steps restore the constraints and the true
+// residual.
 //
 // Constraint rows: node k contributes v_k to the row of each of its four adjacent elements;
 // row (j, q) of continuum j and sub-block q = by P + bx has index j P^2 + q. A thread's
@@ -52,7 +56,8 @@
 // column c+1, whose owner is lane c+1, and is handed over with one shfl_up. Rows per thread
 // divide the sub-block size m = n / P (a power of two; P need not be), so all south elements
 // of a strip lie in one sub-block row; only the north elements of the strip's last row can
-// fall in the next one, and those go straight to shared-memory atomics.
+// fall in the next one, and those go through the same warp reduction with the next row's
+// bins (flush_next).
 #pragma once
 
 #include <cooperative_groups.h>
