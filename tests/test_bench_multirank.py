@@ -51,3 +51,28 @@ def test_single_rank_helpers():
     import bench
     assert bench.max_over_ranks(2.5, None, None) == 2.5
     assert bench.whole_job_rate(10, 1, 3, 2.0) == 15.0
+
+
+def test_level_traffic_record_matches_kernel_sources():
+    """The stored ncu DRAM traffic of the level kernel is reported only for the kernel
+    sources it was captured on and for launch shapes that have a capture."""
+    sys.path.insert(0, ROOT)
+    import bench
+    import mch_inputs as mi
+    wl = mi.workload(bench.WORKLOAD)
+    rec = bench.LEVEL_TRAFFIC[bench.WORKLOAD]
+    # the committed record belongs to the committed level-kernel sources
+    assert rec["sha256_16"] == bench._sources_hash()
+    shapes = [(wl.n_level(k + 1), v) for k, v in enumerate((2, 5, 9, 5))]
+    mean, per = bench._level_traffic(wl, [v for _, v in shapes])
+    assert per == [rec["bytes_per_launch"][s] for s in shapes]
+    assert abs(mean - sum(per) / len(per)) < 1e-6
+    # a shape without a capture gives no traffic
+    assert bench._level_traffic(wl, [0, 0, 0, 0]) == (None, None)
+    # another source hash (an edited kernel) gives none either
+    saved = rec["sha256_16"]
+    try:
+        rec["sha256_16"] = "0" * 16
+        assert bench._level_traffic(wl, [v for _, v in shapes]) == (None, None)
+    finally:
+        rec["sha256_16"] = saved
