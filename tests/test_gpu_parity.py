@@ -12,7 +12,7 @@ import pytest
 
 import mch_inputs as mi
 from oracle import cell, plan
-from util import block_rel_err
+from util import block_rel_err, entry_rel_err
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -57,6 +57,8 @@ def test_level1_4x4_n32(precision, tol):
     Eo = _run_oracle(wl)
     err = block_rel_err(Eg[0], Eo[0]["E"], wl.n_cont, wl.dim)
     assert err < tol, err
+    # every entry on its own, against its Cauchy-Schwarz scale
+    assert entry_rel_err(Eg[0], Eo[0]["E"]) < tol
 
 
 @pytest.mark.parametrize("name,n_fine,macro,strides", [
@@ -74,6 +76,9 @@ def test_hierarchy_small(name, n_fine, macro, strides, precision):
     for lev in range(wl.n_levels):
         err = block_rel_err(Eg[lev], Eo[lev]["E"], wl.n_cont, wl.dim)
         assert err < 1e-9, (lev + 1, err)
+        # every entry on its own, against its Cauchy-Schwarz scale
+        err_e = entry_rel_err(Eg[lev], Eo[lev]["E"])
+        assert err_e < 1e-9, (lev + 1, err_e)
     # the cell functions on the level-1 grid
     for lev in range(1, wl.n_levels + 1):
         phi = s.cell_functions(lev)

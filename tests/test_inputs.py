@@ -63,3 +63,21 @@ def test_misaligned_rve_is_refused():
                            origin=0.01)
     with pytest.raises(ValueError):
         mi.media(wl, np.array([[1, 1]]), 32)
+
+
+def test_entry_rel_err_sees_a_small_entry():
+    """The entry-wise comparison of Gram matrices flags an error in an entry that is small
+    next to its block (which the block-relative norm can hide)."""
+    import numpy as np
+    from util import block_rel_err, entry_rel_err
+    rng = np.random.default_rng(0)
+    B = rng.standard_normal((6, 6))
+    E = B @ B.T + 6 * np.eye(6)
+    E[0, 1] = E[1, 0] = 1e-6 * np.sqrt(E[0, 0] * E[1, 1])   # a small entry
+    F = E.copy()
+    F[0, 1] = F[1, 0] = E[0, 1] + 1e-8 * np.sqrt(E[0, 0] * E[1, 1])
+    assert entry_rel_err(E, E) == 0.0
+    assert abs(entry_rel_err(F, E) - 1e-8) < 1e-12
+    # the same error is below a block norm's reach at this size (2 continua, d = 2: the 2x2
+    # exchange block holds the entry together with its large diagonal)
+    assert block_rel_err(F[None], E[None], 2, 2) < 2e-8

@@ -25,3 +25,14 @@ def block_rel_err(E, Eref, N, d):
             if (~ok).any():
                 worst = max(worst, float(num[~ok].max()))
     return worst
+
+
+def entry_rel_err(E, Eref):
+    """max over points and entries of |dE_rs| / sqrt(Eref_rr Eref_ss): every entry of the
+    (symmetric positive definite) Gram matrix against its Cauchy-Schwarz bound |E_rs| <=
+    sqrt(E_rr E_ss), so that a small entry inside a block is checked on its own."""
+    E = np.asarray(E).reshape(-1, *np.asarray(E).shape[-2:])
+    Eref = np.asarray(Eref).reshape(E.shape)
+    d = np.sqrt(np.abs(np.einsum("pii->pi", Eref)))
+    scale = d[:, :, None] * d[:, None, :]
+    return float((np.abs(E - Eref) / scale).max())
